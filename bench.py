@@ -1,0 +1,411 @@
+#!/usr/bin/env python
+"""Benchmark of the windowed beamspace MVDR hot path on GB300.
+
+One step = one whole pass of the path over one synthetic batch: channelise
+(F-point FFT of every element of every record), beamspace + window gather
+(zero-padded M-point spatial FFT), loaded window covariance, Cholesky MVDR
+solve and apply, for every (target, subband) pair.  Metric: (target,
+subband) MVDR solves per second = pairs / step time.
+
+Default workload: N=1024 elements, F=2048, L=128 subbands, M=2048, W=9,
+K=512, T=64 targets (8192 pairs), 32 training + 8 test records (671 MB raw
+cube, larger than L2, so no flush is needed between steps).
+
+Arms:  --impl ours (default): the CUDA path through the C ABI.
+       --impl reference: the FP64 CPU oracle on the host cores, one bounded
+       sample of the workload per step.
+Under torchrun every rank runs its own batch (independent problems, weak
+scaling, no data-path collective); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from synth import all_configs, make_scene  # noqa: E402
+
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="C3")
+    ap.add_argument("--precision", choices=["fp32", "fp16", "bf16"], default="fp32")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="budget of the oracle sample timed for cpu_baseline")
+    return ap.parse_args()
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return d, "measured"
+    return PEAKS_FALLBACK, "fallback"
+
+
+def workload_desc(cfg):
+    return {
+        "workload": f"{cfg.name}: {cfg.description}",
+        "pairs": cfg.pairs, "N": cfg.N, "F": cfg.F, "L": cfg.L, "M": cfg.M, "T": cfg.T,
+        "W": cfg.W[0] if len(set(cfg.W)) == 1 else "per-target",
+        "K": cfg.K[0] if len(set(cfg.K)) == 1 else "per-target",
+        "P_train": cfg.P_tr, "P_test": cfg.P_te,
+        "l2": "no flush: raw cube %.0f MB > 129 MB L2" % (cfg.P * cfg.F * cfg.N * 8 / 1e6),
+    }
+
+
+# --------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except FileNotFoundError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# --------------------------------------------------------------- distributed
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(ws, value: float) -> float:
+    if ws == 1:
+        return value
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# --------------------------------------------------------------- oracle leg
+def oracle_sample(cfg, scene, seconds: float, subband_order=None):
+    """Run the oracle subband by subband (all targets) until `seconds` pass.
+    Returns (pairs done, elapsed seconds, results by subband)."""
+    import oracle as O
+    order = subband_order if subband_order is not None else list(range(cfg.L))
+    done, results = 0, {}
+    t0 = time.perf_counter()
+    for s in order:
+        res = O.run_pipeline(scene.x, cfg, scene.u_tgt, subbands=[s])
+        results[s] = res
+        done += len(res.pairs.t)
+        if time.perf_counter() - t0 >= seconds:
+            break
+    return done, time.perf_counter() - t0, results
+
+
+def run_reference(args):
+    ws, rank, _ = dist_init()
+    cfg = all_configs()[args.workload]
+    if rank != 0:
+        return
+    scene = make_scene(cfg)
+    import oracle as O
+    times, pairs = [], []
+    order = [(7 * i) % cfg.L for i in range(args.warmup + args.steps)]
+    for i, s in enumerate(order):
+        t0 = time.perf_counter()
+        res = O.run_pipeline(scene.x, cfg, scene.u_tgt, subbands=[s])
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+            pairs.append(len(res.pairs.t))
+    value = sum(pairs) / sum(times)
+    cores = os.cpu_count()
+    sample = (f"one subband (all {cfg.T} targets, all records and elements) per step; "
+              f"value = pairs / oracle time")
+    line = {
+        "impl": "reference", "metric": "(target,subband) MVDR solves/sec", "value": value,
+        "unit": "pairs/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * float(np.mean(times)), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_desc(cfg),
+        "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------- our arm
+def algorithmic_bytes(plan, cfg):
+    s = plan.sizes
+    raw = cfg.P * cfg.F * cfg.N * 8
+    return {
+        "channelize": 2 * raw,
+        "beamspace": raw + s.ztrain_bytes + 8 * s.ztest_elems,
+        "window_cov": s.ztrain_bytes + 16 * s.r_elems,
+        "mvdr_solve": 16 * s.r_elems + 24 * s.c_elems + 8 * s.c_elems + 4 * s.pairs,
+        "apply": 8 * s.ztest_elems + 8 * s.c_elems + 8 * s.out_elems,
+    }
+
+
+def kernel_traffic(stage):
+    """DRAM bytes per launch of a stage from the committed ncu summary, if the
+    kernel source has not changed since it was taken (else None)."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        d = json.load(fh)
+    ent = d.get(stage)
+    if not ent:
+        return None
+    src = os.path.join(ROOT, ent["source"])
+    if not os.path.exists(src):
+        return None
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    return ent["bytes_per_launch"] if h == ent["source_sha256_16"] else None
+
+
+def run_ours(args):
+    ws, rank, local = dist_init()
+    import paper_2508_11790_gb300 as P
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    cfg = all_configs()[args.workload]
+    scene = make_scene(cfg)
+    prec = {"fp32": P.BS_PREC_FP32, "fp16": P.BS_PREC_FP16, "bf16": P.BS_PREC_BF16}[args.precision]
+    plan = P.Plan.from_scene_config(cfg, scene.u_tgt, precision=prec)
+    b = P.alloc_buffers(plan, dev)
+    b.x.copy_(torch.from_numpy(scene.x.reshape(-1)))
+    stream = torch.cuda.Stream(dev)
+
+    def stages_for(pl, bb):
+        return [
+            ("channelize", lambda: P.bs_channelize(pl, bb.x, bb.xc, stream=stream)),
+            ("beamspace", lambda: P.bs_beamspace(pl, bb.xc, bb.z_train, bb.z_test, stream=stream)),
+            ("window_cov", lambda: P.bs_window_cov(pl, bb.z_train, bb.R, stream=stream)),
+            ("mvdr_solve", lambda: P.bs_mvdr_solve(pl, bb.R, bb.c, bb.info, stream=stream)),
+            ("apply", lambda: P.bs_apply(pl, bb.z_test, bb.c, bb.out, stream=stream)),
+        ]
+
+    stages = stages_for(plan, b)
+
+    def step():
+        P.bs_run(plan, b, stream=stream)
+
+    def timed_loop(fn, K):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier(ws)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for _ in range(K):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier(ws)
+        return e0.elapsed_time(e1)
+
+    def stage_breakdown(stg, K):
+        ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in stg] for _ in range(K)]
+        torch.cuda.synchronize(dev)
+        for k in range(K):
+            for (name, fn), (a, z) in zip(stg, ev[k]):
+                a.record(stream)
+                fn()
+                z.record(stream)
+        torch.cuda.synchronize(dev)
+        return {name: float(np.mean([ev[k][i][0].elapsed_time(ev[k][i][1]) for k in range(K)]))
+                for i, (name, _) in enumerate(stg)}
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+
+    sampler = ClockSampler(dev.index)
+    sampler.start()
+    total_ms = timed_loop(step, args.steps)
+    clocks = sampler.stop()
+    ms_step = max_over_ranks(ws, total_ms / args.steps)
+    value = ws * cfg.pairs / (ms_step / 1e3)
+
+    breakdown = stage_breakdown(stages, args.steps)
+    info = b.info.cpu().numpy()
+    peaks, peak_kind = load_peaks()
+    abytes = algorithmic_bytes(plan, cfg)
+    dom = max(breakdown, key=breakdown.get)
+    achieved = abytes[dom] / (breakdown[dom] / 1e3) / 1e9
+    roofline = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": kernel_traffic(dom),
+                "peak_source": f"{peak_kind} HBM copy bandwidth",
+                "algorithmic_bytes": abytes[dom]}
+    per_stage = {k: {"ms": v, "GB/s": abytes[k] / (v / 1e3) / 1e9,
+                     "frac_hbm": abytes[k] / (v / 1e3) / 1e9 / peaks["hbm_gbs"]}
+                 for k, v in breakdown.items()}
+    solve_core_ms = breakdown["window_cov"] + breakdown["mvdr_solve"]
+
+    plain = None
+    if not args.no_plain:
+        pplan = P.Plan.from_scene_config(cfg, scene.u_tgt, precision=P.BS_PREC_FP32,
+                                         flags=P.BS_FLAG_PLAIN)
+        pb = P.alloc_buffers(pplan, dev)
+        pb.x.copy_(b.x)
+        for _ in range(args.warmup):
+            P.bs_run(pplan, pb, stream=stream)
+        pms = timed_loop(lambda: P.bs_run(pplan, pb, stream=stream), args.steps) / args.steps
+        pbd = stage_breakdown(stages_for(pplan, pb), max(3, args.steps // 4))
+        p_core = pbd["window_cov"] + pbd["mvdr_solve"]
+        plain = {"ms_per_step": pms, "value": cfg.pairs / (pms / 1e3),
+                 "solve_core_ms": p_core, "solve_core_pairs_per_s": cfg.pairs / (p_core / 1e3),
+                 "solve_core_speedup_of_ours": p_core / solve_core_ms,
+                 "step_speedup_of_ours": pms / (ms_step)}
+        del pb, pplan
+
+    e2e = None
+    if not args.no_e2e:
+        xh = torch.from_numpy(scene.x.reshape(-1)).pin_memory()
+        oh = torch.empty(plan.sizes.out_elems, dtype=torch.complex64).pin_memory()
+        with torch.cuda.stream(stream):
+            for _ in range(2):
+                P.bs_run_host(plan, xh, oh, b, stream=stream)
+            barrier(ws)
+            t0 = time.perf_counter()
+            for _ in range(args.steps):
+                P.bs_run_host(plan, xh, oh, b, stream=stream)
+            dt = (time.perf_counter() - t0) / args.steps
+        dt = max_over_ranks(ws, dt)
+        e2e = {"value": ws * cfg.pairs / dt, "unit": "pairs/s",
+               "h2d_bytes_per_step": xh.numel() * 8, "d2h_bytes_per_step": oh.numel() * 8,
+               "ms_per_step": dt * 1e3}
+
+    cpu = None
+    accuracy = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        order = [0, cfg.L // 2, cfg.L - 1] + [s for s in range(1, cfg.L) if s not in (cfg.L // 2, cfg.L - 1)]
+        done, el, results = oracle_sample(cfg, scene, args.cpu_seconds, order)
+        cpu = {"value": done / el, "unit": "pairs/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"{len(results)} subband(s) x {cfg.T} targets = {done} pairs of the same "
+                         f"workload (all records and elements), FP64 numpy, {el:.1f} s"}
+        import oracle as O
+        off = plan.offsets()
+        cc = b.c.cpu().numpy()
+        errs, losses = [], []
+        for s, res in results.items():
+            for k in range(len(res.pairs.t)):
+                g = int(res.pairs.t[k]) * cfg.L + int(res.pairs.s[k])
+                cg = cc[off["woff"][g]:off["woff"][g + 1]].astype(np.complex128)
+                errs.append(float(np.linalg.norm(cg - res.c[k]) / np.linalg.norm(res.c[k])))
+                losses.append(abs(O.sinr_loss_db(cg, res.c[k], res.pairs.a_tilde[k], res.R[k])))
+        accuracy = {"pairs_checked": len(errs), "max_weight_rel_err": max(errs),
+                    "median_weight_rel_err": float(np.median(errs)),
+                    "max_abs_sinr_loss_db": max(losses)}
+
+    if rank == 0:
+        dtype = {"fp32": "f32", "fp16": "f16 windows, f32/f64 solve", "bf16": "bf16 windows, f32/f64 solve"}[args.precision]
+        line = {
+            "metric": "(target,subband) MVDR solves/sec", "value": value, "unit": "pairs/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": dtype, "data": "synthetic",
+            "config": dict(workload_desc(cfg), precision=args.precision,
+                           parallelism=f"{ws} independent batch(es)"),
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": len(stages) * args.steps,
+            "clocks": clocks, "stages": per_stage, "solve_core_ms": solve_core_ms,
+            "plain_fp32": plain, "accuracy": accuracy,
+            "info_counts": {str(k): int(v) for k, v in zip(*np.unique(info, return_counts=True))},
+        }
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+    if int(os.environ.get("WORLD_SIZE", "1")) > 1:
+        import torch.distributed as dist
+        if dist.is_initialized():
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

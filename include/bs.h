@@ -1,0 +1,226 @@
+/*
+ * bs.h - C ABI of the windowed beamspace MVDR hot path on GB300 (sm_103a).
+ *
+ * Method: "Scaling Wideband Massive MIMO Radar via Beamspace Dimension
+ * Reduction" (arXiv 2508.11790).  Per record the array data are channelised
+ * into L subbands by an F-point FFT (Sec. III-A), each subband vector is
+ * taken to beamspace by a zero-padded M-point spatial DFT (Eq. VerDFT,
+ * Eq. BeamTransform), a W-beam window is cut around every target's
+ * frequency-squinted beam (Eq. SubOmegaX, Eq. OverallWindow,
+ * Eq. ApplyWindow), the windowed training vectors give a diagonally loaded
+ * W x W covariance (Eq. EmpiricalCov), the MVDR correlator
+ * c = R^-1 a / (a^H R^-1 a) is solved per (target, subband) pair
+ * (Eq. BeamCorrMVDR) and applied to the test vectors as c^H y (Sec. II-B).
+ * The array is a half-wavelength uniform linear array (the paper's planar
+ * array with N_z = 1), so the beamspace transform is one truncated DFT.
+ *
+ * Conventions (all entry points):
+ *  - Data pointers are DEVICE pointers owned by the caller, except where a
+ *    name ends in _host.  The library never allocates or frees on the hot
+ *    path; a plan owns its small tables and workspace, allocated at create.
+ *  - Calls are asynchronous on the given stream (NULL = legacy default
+ *    stream).  Argument and launch errors are returned at once; numerical
+ *    failures are reported per pair in `info` (bs_mvdr_solve).
+ *  - Complex values are interleaved (re, im) pairs, C-contiguous.
+ *  - Pair index g = t * L + s for target t and subband s.  Subband s is the
+ *    paper's l = s - L/2 + 1 with centre f(l) = f_c + ((l - 1/2)/L) f_s
+ *    (Eq. SubChannelFreq); s = 0 is the lowest.
+ *  - "vector" v of a pair is record p, bin i of its subband, v = p*B + i
+ *    (record-major), B = F / L.  Training vectors are those of the first
+ *    P_train records; the first K_t of them enter the covariance of every
+ *    pair of target t.  Test vectors are those of the next P_test records,
+ *    v' = (p - P_train) * B + i.
+ *  - Ragged per-pair arrays are packed back to back in pair order:
+ *      weights / steering : W_g complex values per pair
+ *      training windows   : K_g * W_g per pair, [v][w]
+ *      test windows       : Vte * W_g per pair, [v'][w], Vte = P_test * B
+ *      covariance         : W_g * W_g per pair, [i][j] row-major
+ *    bs_plan_sizes() returns the totals and bs_plan_offsets() the offsets.
+ *  - Not thread-safe per plan if two threads launch on one plan with
+ *    different buffers at the same time (plan workspace is shared).
+ */
+#ifndef BS_H
+#define BS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *bs_stream; /* same handle as cudaStream_t */
+
+typedef enum {
+    BS_OK = 0,
+    BS_EINVAL = 1,        /* bad argument (message in bs_last_error()) */
+    BS_ENOMEM = 2,        /* device allocation failed at plan create */
+    BS_ECUDA = 3,         /* CUDA runtime error (message in bs_last_error()) */
+    BS_ENOTPD = 4,        /* reserved: reported per pair through info */
+    BS_ETIMEOUT = 5,      /* a bounded device wait gave up */
+    BS_EUNSUPPORTED = 6   /* size outside the compiled kernel range */
+} bs_status;
+
+/* Storage / arithmetic precision of the training windows and covariance. */
+typedef enum {
+    BS_PREC_FP32 = 0,     /* cf32 windows, FP32 SIMT products */
+    BS_PREC_FP16 = 1,     /* fp16 windows (x store_scale), tensor-core products */
+    BS_PREC_BF16 = 2      /* bf16 windows, tensor-core products */
+} bs_precision;
+
+/* Plan flags. */
+#define BS_FLAG_PLAIN      (1u << 0) /* plain FP32 per-pair path: one CTA per pair,
+                                        FP32 sums, FP32 Cholesky, no refinement */
+#define BS_FLAG_NO_REFINE  (1u << 1) /* skip the iterative-refinement step */
+#define BS_FLAG_NO_FP64    (1u << 2) /* never escalate a pair to the FP64 solve */
+
+typedef struct { float re, im; } bs_cf32;
+typedef struct { double re, im; } bs_cf64;
+
+typedef struct {
+    int32_t N;        /* array elements, 1..4096 */
+    int32_t F;        /* fast-time samples per record; power of 2, 16..4096 */
+    int32_t L;        /* subbands; power of 2 dividing F */
+    int32_t M;        /* spatial FFT size; power of 2, N <= M <= 4096 */
+    int32_t T;        /* targets, >= 1 */
+    int32_t P_train;  /* target-free training records, >= 1 */
+    int32_t P_test;   /* test records, >= 0 */
+    double fc;        /* carrier frequency, Hz */
+    double fs;        /* sampling rate, Hz */
+    double fd;        /* design frequency of the lambda/2 spacing, Hz */
+    const double  *u; /* [T] host: direction sine sin(phi_t) of each target */
+    const int32_t *W; /* [T] host: window size per target, 1..16 */
+    const int32_t *K; /* [T] host: training vectors per target, 1..P_train*B */
+    double delta;     /* diagonal loading added to every window covariance */
+    int32_t precision;   /* bs_precision */
+    uint32_t flags;      /* BS_FLAG_* */
+    double kappa_max;    /* FP64 escalation threshold on the Cholesky pivot
+                            ratio (max L_ii / min L_ii)^2; <= 0 selects 1e5 */
+    float store_scale;   /* 16-bit windows hold value * store_scale (<= 0: 1) */
+} bs_config;
+
+typedef struct {
+    int64_t pairs;        /* T * L */
+    int32_t B;            /* bins per subband, F / L */
+    int32_t Vte;          /* test vectors per pair, P_test * B */
+    int32_t W_max, K_max;
+    int64_t x_elems;      /* cf32 elements of one raw cube, P*F*N, P = P_train+P_test */
+    int64_t xc_elems;     /* cf32 elements of the channelised cube, P*F*N */
+    int64_t ztrain_elems; /* complex elements of the training windows, sum W_g K_g */
+    int64_t ztrain_bytes; /* bytes: 8 per element (FP32) or 4 (FP16/BF16) */
+    int64_t ztest_elems;  /* cf32 elements of the test windows, sum W_g Vte */
+    int64_t r_elems;      /* cf64 elements of the covariances, sum W_g^2 */
+    int64_t c_elems;      /* cf32 elements of the weights, sum W_g */
+    int64_t out_elems;    /* cf32 elements of the output, pairs * Vte */
+} bs_sizes;
+
+/* Buffers of one whole pass, for bs_run / bs_run_host (device pointers). */
+typedef struct {
+    bs_cf32 *x;        /* [P][F][N] raw IQ (bs_run_host copies the host cube here) */
+    bs_cf32 *xc;       /* [P][F][N] channelised */
+    void    *z_train;  /* training windows */
+    bs_cf32 *z_test;   /* test windows */
+    bs_cf64 *R;        /* covariances */
+    bs_cf32 *c;        /* weights */
+    int32_t *info;     /* [pairs] */
+    bs_cf32 *out;      /* [pairs][Vte] */
+} bs_buffers;
+
+typedef struct bs_plan bs_plan;
+
+/* ---------------------------------------------------------------- plan --- */
+
+/* Create a plan on the current CUDA device.  Computes in FP64 on the host,
+ * per pair: the squinted spatial frequency Omega = pi*u*(f(l)/f_d)
+ * (Eq. SubOmegaX), x = Omega*M/(2*pi), the window start
+ * floor(x - W/2 + 1) mod M (the W consecutive beams whose centre is nearest
+ * to x; evaluated in exactly this order with no fused multiply-add), and
+ * the windowed steering vector a~ = S D a(Omega) (Sec. III-C) from the
+ * closed-form Dirichlet kernel.  Uploads these tables.
+ * Errors: BS_EINVAL (sizes, NULL pointers), BS_EUNSUPPORTED, BS_ENOMEM,
+ * BS_ECUDA.  On error *plan is NULL. */
+bs_status bs_plan_create(bs_plan **plan, const bs_config *cfg);
+void      bs_plan_destroy(bs_plan *plan);
+bs_status bs_plan_sizes(const bs_plan *plan, bs_sizes *out);
+
+/* Host copies of the per-pair tables (any pointer may be NULL):
+ * start[pairs] window start beam; W[pairs], K[pairs]; woff[pairs+1],
+ * ztr_off[pairs+1], zte_off[pairs+1], roff[pairs+1] element offsets of the
+ * packed arrays; a_tilde[c_elems] windowed steering vectors (FP64). */
+bs_status bs_plan_offsets(const bs_plan *plan, int32_t *start, int32_t *W, int32_t *K,
+                          int64_t *woff, int64_t *ztr_off, int64_t *zte_off,
+                          int64_t *roff, bs_cf64 *a_tilde);
+
+/* The same per-pair tables as bs_plan_create, computed on the host only (no
+ * device is touched): start[T*L] window start beams and a_tilde[sum W_g]
+ * windowed steering vectors (pair order, W_g values each).  Either output
+ * may be NULL.  Errors: as bs_plan_create's argument checks. */
+bs_status bs_plan_tables_host(const bs_config *cfg, int32_t *start, bs_cf64 *a_tilde);
+
+/* ----------------------------------------------------------- hot path --- */
+
+/* Channelise (Sec. III-A): for every record p < P and element n,
+ *   xc[p][s*B + i][n] = F^-1/2 sum_t x[p][t][n] e^{-j 2 pi k t / F}
+ * with k = ((s - L/2) B + i) mod F.  x, xc: [P][F][N] cf32, distinct. */
+bs_status bs_channelize(const bs_plan *plan, const bs_cf32 *x, int32_t P,
+                        bs_cf32 *xc, bs_stream stream);
+
+/* Beamspace + window (Eq. BeamTransform, Eq. ApplyWindow): for every record
+ * p < P_train + P_test and bin q = s*B + i, y^ = M^-1/2 sum_{n<N}
+ * xc[p][q][n] e^{-j 2 pi m n / M} (zero-padded to M), then for every target
+ * t the W_t beams (start_g + w) mod M, g = t*L + s, are written:
+ *   training records (p < P_train), v = p*B + i < K_t : z_train, in the
+ *     plan precision (FP16 / BF16 hold value * store_scale);
+ *   test records: z_test (cf32).
+ * z_test may be NULL when P_test == 0. */
+bs_status bs_beamspace(const bs_plan *plan, const bs_cf32 *xc, void *z_train,
+                       bs_cf32 *z_test, bs_stream stream);
+
+/* Full zero-padded beamspace transform of nvec vectors (Eq. BeamTransform
+ * without the window): yb[v][m] = M^-1/2 sum_{n<N} y[v][n] e^{-j2pi mn/M}.
+ * y: [nvec][N] cf32, yb: [nvec][M] cf32. */
+bs_status bs_beamspace_full(const bs_plan *plan, const bs_cf32 *y, int64_t nvec,
+                            bs_cf32 *yb, bs_stream stream);
+
+/* Loaded window covariance (Eq. EmpiricalCov on the windowed vectors, plus
+ * loading): R_g = (1/K_g) sum_{v<K_g} z_v z_v^H + delta_g I, stored in FP64
+ * (full Hermitian matrix).  delta_pair: NULL = plan delta, else a device
+ * array [pairs] of per-pair loading (float).  Products are formed in the
+ * plan precision; FP32 partial sums of at most 16 vectors are combined in
+ * double-float. */
+bs_status bs_window_cov(const bs_plan *plan, const void *z_train, const float *delta_pair,
+                        bs_cf64 *R, bs_stream stream);
+
+/* MVDR correlator (Eq. BeamCorrMVDR): c_g = R_g^-1 a~_g / (a~_g^H R_g^-1 a~_g).
+ * FP32 Cholesky R = L L^H and two triangular solves, one refinement step
+ * with the residual a~ - R v in FP64, normalisation in FP64.  Pairs whose
+ * pivot ratio (max L_ii / min L_ii)^2 exceeds kappa_max, or whose FP32
+ * factorisation fails, are solved again entirely in FP64.
+ * info[g]: 0 = FP32 solve, -2 = solved in FP64, -1 = non-finite input,
+ * k >= 1 = pivot k-1 not positive in FP64 (c_g set to NaN). */
+bs_status bs_mvdr_solve(const bs_plan *plan, const bs_cf64 *R, bs_cf32 *c, int32_t *info,
+                        bs_stream stream);
+
+/* Beamformer output (Sec. II-B): out[g][v'] = c_g^H z_test[g][v'], v' < Vte. */
+bs_status bs_apply(const bs_plan *plan, const bs_cf32 *z_test, const bs_cf32 *c,
+                   bs_cf32 *out, bs_stream stream);
+
+/* The whole pass on device buffers: channelise, beamspace, covariance,
+ * solve, apply (delta = plan delta). */
+bs_status bs_run(const bs_plan *plan, const bs_buffers *buf, bs_stream stream);
+
+/* The whole pass from host memory: copies x_host ([P][F][N] cf32; pinned
+ * memory makes the copy asynchronous and fast) into the device buffer
+ * buf->x, runs bs_run, and copies buf->out back to out_host ([pairs][Vte]).
+ * Synchronises `stream` before returning. */
+bs_status bs_run_host(const bs_plan *plan, const bs_cf32 *x_host, bs_cf32 *out_host,
+                      const bs_buffers *buf, bs_stream stream);
+
+/* ------------------------------------------------------------- errors --- */
+const char *bs_status_string(bs_status s);
+const char *bs_last_error(void);   /* thread-local text of the last error */
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BS_H */

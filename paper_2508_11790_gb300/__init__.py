@@ -1,0 +1,343 @@
+"""Windowed beamspace MVDR hot path on GB300: Python binding of the C ABI.
+
+The functions here have the names of the C entry points in ``include/bs.h``
+and only marshal arguments: every step of the path runs in the CUDA kernels
+of ``libbs_mvdr.so``.  PyTorch supplies device memory and streams.  If the
+library is missing the import fails with an error; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import Optional, Sequence
+
+import numpy as np
+import torch
+
+from .build import lib_path
+
+__all__ = [
+    "BS_PREC_FP32", "BS_PREC_FP16", "BS_PREC_BF16",
+    "BS_FLAG_PLAIN", "BS_FLAG_NO_REFINE", "BS_FLAG_NO_FP64",
+    "BsError", "Plan", "Buffers", "alloc_buffers", "lib", "bs_plan_tables_host",
+    "bs_channelize", "bs_beamspace", "bs_beamspace_full", "bs_window_cov",
+    "bs_mvdr_solve", "bs_apply", "bs_run", "bs_run_host",
+]
+
+BS_PREC_FP32, BS_PREC_FP16, BS_PREC_BF16 = 0, 1, 2
+BS_FLAG_PLAIN, BS_FLAG_NO_REFINE, BS_FLAG_NO_FP64 = 1, 2, 4
+
+
+class BsError(RuntimeError):
+    pass
+
+
+class _Config(ctypes.Structure):
+    _fields_ = [
+        ("N", ctypes.c_int32), ("F", ctypes.c_int32), ("L", ctypes.c_int32),
+        ("M", ctypes.c_int32), ("T", ctypes.c_int32), ("P_train", ctypes.c_int32),
+        ("P_test", ctypes.c_int32), ("fc", ctypes.c_double), ("fs", ctypes.c_double),
+        ("fd", ctypes.c_double), ("u", ctypes.POINTER(ctypes.c_double)),
+        ("W", ctypes.POINTER(ctypes.c_int32)), ("K", ctypes.POINTER(ctypes.c_int32)),
+        ("delta", ctypes.c_double), ("precision", ctypes.c_int32), ("flags", ctypes.c_uint32),
+        ("kappa_max", ctypes.c_double), ("store_scale", ctypes.c_float),
+    ]
+
+
+class _Sizes(ctypes.Structure):
+    _fields_ = [
+        ("pairs", ctypes.c_int64), ("B", ctypes.c_int32), ("Vte", ctypes.c_int32),
+        ("W_max", ctypes.c_int32), ("K_max", ctypes.c_int32), ("x_elems", ctypes.c_int64),
+        ("xc_elems", ctypes.c_int64), ("ztrain_elems", ctypes.c_int64),
+        ("ztrain_bytes", ctypes.c_int64), ("ztest_elems", ctypes.c_int64),
+        ("r_elems", ctypes.c_int64), ("c_elems", ctypes.c_int64), ("out_elems", ctypes.c_int64),
+    ]
+
+
+class _Buffers(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_void_p) for n in ("x", "xc", "z_train", "z_test", "R", "c", "info", "out")]
+
+
+_P = ctypes.c_void_p
+_SIGS = {
+    "bs_plan_create": ([ctypes.POINTER(_P), ctypes.POINTER(_Config)], ctypes.c_int),
+    "bs_plan_destroy": ([_P], None),
+    "bs_plan_sizes": ([_P, ctypes.POINTER(_Sizes)], ctypes.c_int),
+    "bs_plan_offsets": ([_P] + [_P] * 8, ctypes.c_int),
+    "bs_channelize": ([_P, _P, ctypes.c_int32, _P, _P], ctypes.c_int),
+    "bs_beamspace": ([_P, _P, _P, _P, _P], ctypes.c_int),
+    "bs_beamspace_full": ([_P, _P, ctypes.c_int64, _P, _P], ctypes.c_int),
+    "bs_window_cov": ([_P, _P, _P, _P, _P], ctypes.c_int),
+    "bs_mvdr_solve": ([_P, _P, _P, _P, _P], ctypes.c_int),
+    "bs_apply": ([_P, _P, _P, _P, _P], ctypes.c_int),
+    "bs_run": ([_P, ctypes.POINTER(_Buffers), _P], ctypes.c_int),
+    "bs_run_host": ([_P, _P, _P, ctypes.POINTER(_Buffers), _P], ctypes.c_int),
+    "bs_plan_tables_host": ([ctypes.POINTER(_Config), _P, _P], ctypes.c_int),
+    "bs_status_string": ([ctypes.c_int], ctypes.c_char_p),
+    "bs_last_error": ([], ctypes.c_char_p),
+}
+
+_lib: Optional[ctypes.CDLL] = None
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded C library (built by ``__graft_entry__.build()``)."""
+    global _lib
+    if _lib is None:
+        path = lib_path()
+        if not os.path.exists(path):
+            raise BsError(f"CUDA library {path} is missing: run "
+                          "`python -m paper_2508_11790_gb300.build` first")
+        L = ctypes.CDLL(path)
+        for name, (args, res) in _SIGS.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def _check(status: int, what: str) -> None:
+    if status != 0:
+        L = lib()
+        raise BsError(f"{what}: {L.bs_status_string(status).decode()} "
+                      f"({L.bs_last_error().decode()})")
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _ptr(t: Optional[torch.Tensor], dtype=None, numel=None, name="buffer") -> Optional[int]:
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise BsError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise BsError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype not in (dtype if isinstance(dtype, tuple) else (dtype,)):
+        raise BsError(f"{name} has dtype {t.dtype}, expected {dtype}")
+    if numel is not None and t.numel() < numel:
+        raise BsError(f"{name} holds {t.numel()} elements, needs {numel}")
+    return t.data_ptr()
+
+
+@dataclass
+class Sizes:
+    pairs: int
+    B: int
+    Vte: int
+    W_max: int
+    K_max: int
+    x_elems: int
+    xc_elems: int
+    ztrain_elems: int
+    ztrain_bytes: int
+    ztest_elems: int
+    r_elems: int
+    c_elems: int
+    out_elems: int
+
+
+def _make_config(N, F, L, M, u, W, K, P_train, P_test, fc, fs, fd, delta, precision=BS_PREC_FP32,
+                 flags=0, kappa_max=0.0, store_scale=0.0):
+    """ctypes config plus the numpy arrays it points into (keep both alive)."""
+    ua = np.ascontiguousarray(u, dtype=np.float64)
+    Wa = np.ascontiguousarray(W, dtype=np.int32)
+    Ka = np.ascontiguousarray(K, dtype=np.int32)
+    cfg = _Config(N, F, L, M, len(ua), P_train, P_test, fc, fs, fd,
+                  ua.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                  Wa.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                  Ka.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                  delta, precision, flags, kappa_max, store_scale)
+    return cfg, (ua, Wa, Ka)
+
+
+def bs_plan_tables_host(**kw):
+    """Window starts [T*L] and windowed steering vectors (packed, complex128)
+    computed by the library on the host (no device needed)."""
+    cfg, keep = _make_config(**kw)
+    G = cfg.T * cfg.L
+    start = np.empty(G, np.int32)
+    at = np.empty(int(np.repeat(keep[1], cfg.L).sum()), np.complex128)
+    _check(lib().bs_plan_tables_host(ctypes.byref(cfg), start.ctypes.data, at.ctypes.data),
+           "bs_plan_tables_host")
+    return start, at
+
+
+class Plan:
+    """A bs_plan: per-pair window tables and steering vectors on the device."""
+
+    def __init__(self, *, N: int, F: int, L: int, M: int, u: Sequence[float],
+                 W: Sequence[int], K: Sequence[int], P_train: int, P_test: int,
+                 fc: float, fs: float, fd: float, delta: float,
+                 precision: int = BS_PREC_FP32, flags: int = 0,
+                 kappa_max: float = 0.0, store_scale: float = 0.0):
+        self.T = len(u)
+        cfg, self._keep = _make_config(N, F, L, M, u, W, K, P_train, P_test, fc, fs, fd, delta,
+                                       precision, flags, kappa_max, store_scale)
+        self.N, self.F, self.L, self.M = N, F, L, M
+        self.P_train, self.P_test = P_train, P_test
+        self.precision, self.flags = precision, flags
+        h = _P()
+        _check(lib().bs_plan_create(ctypes.byref(h), ctypes.byref(cfg)), "bs_plan_create")
+        self._h = h
+        s = _Sizes()
+        _check(lib().bs_plan_sizes(h, ctypes.byref(s)), "bs_plan_sizes")
+        self.sizes = Sizes(**{f: getattr(s, f) for f, _ in _Sizes._fields_})
+
+    @classmethod
+    def from_scene_config(cls, cfg, u, precision=BS_PREC_FP32, flags=0, **kw):
+        """Plan for a ``synth.SceneConfig`` workload with target sines u."""
+        return cls(N=cfg.N, F=cfg.F, L=cfg.L, M=cfg.M, u=u, W=cfg.W, K=cfg.K,
+                   P_train=cfg.P_tr, P_test=cfg.P_te, fc=cfg.fc, fs=cfg.fs, fd=cfg.fd,
+                   delta=cfg.delta, precision=precision, flags=flags, **kw)
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def P(self) -> int:
+        return self.P_train + self.P_test
+
+    def offsets(self) -> dict:
+        G = self.sizes.pairs
+        out = {
+            "start": np.empty(G, np.int32), "W": np.empty(G, np.int32), "K": np.empty(G, np.int32),
+            "woff": np.empty(G + 1, np.int64), "ztr_off": np.empty(G + 1, np.int64),
+            "zte_off": np.empty(G + 1, np.int64), "roff": np.empty(G + 1, np.int64),
+            "a_tilde": np.empty(self.sizes.c_elems, np.complex128),
+        }
+        args = [out[k].ctypes.data for k in ("start", "W", "K", "woff", "ztr_off", "zte_off", "roff", "a_tilde")]
+        _check(lib().bs_plan_offsets(self._h, *args), "bs_plan_offsets")
+        return out
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            lib().bs_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _ztrain_dtype(plan: Plan):
+    return torch.complex64 if plan.precision == BS_PREC_FP32 else (
+        torch.float16 if plan.precision == BS_PREC_FP16 else torch.bfloat16)
+
+
+@dataclass
+class Buffers:
+    x: torch.Tensor
+    xc: torch.Tensor
+    z_train: torch.Tensor
+    z_test: torch.Tensor
+    R: torch.Tensor
+    c: torch.Tensor
+    info: torch.Tensor
+    out: torch.Tensor
+
+
+def alloc_buffers(plan: Plan, device="cuda") -> Buffers:
+    """Caller-owned device buffers of one whole pass (allocated by torch)."""
+    s = plan.sizes
+    zt = _ztrain_dtype(plan)
+    ztr = (torch.empty(s.ztrain_elems, dtype=zt, device=device) if zt == torch.complex64
+           else torch.empty(s.ztrain_elems * 2, dtype=zt, device=device))
+    return Buffers(
+        x=torch.empty(s.x_elems, dtype=torch.complex64, device=device),
+        xc=torch.empty(s.xc_elems, dtype=torch.complex64, device=device),
+        z_train=ztr,
+        z_test=torch.empty(max(s.ztest_elems, 1), dtype=torch.complex64, device=device),
+        R=torch.empty(s.r_elems, dtype=torch.complex128, device=device),
+        c=torch.empty(s.c_elems, dtype=torch.complex64, device=device),
+        info=torch.empty(s.pairs, dtype=torch.int32, device=device),
+        out=torch.empty(max(s.out_elems, 1), dtype=torch.complex64, device=device),
+    )
+
+
+def _ztr_check(plan: Plan, z: torch.Tensor, name="z_train") -> int:
+    s = plan.sizes
+    dt = _ztrain_dtype(plan)
+    n = s.ztrain_elems if dt == torch.complex64 else 2 * s.ztrain_elems
+    return _ptr(z, dt, n, name)
+
+
+def bs_channelize(plan: Plan, x: torch.Tensor, xc: torch.Tensor, P: Optional[int] = None, stream=None):
+    P = plan.P if P is None else P
+    n = P * plan.F * plan.N
+    _check(lib().bs_channelize(plan.handle, _ptr(x, torch.complex64, n, "x"), P,
+                               _ptr(xc, torch.complex64, n, "xc"), _stream(stream)), "bs_channelize")
+
+
+def bs_beamspace(plan: Plan, xc: torch.Tensor, z_train: torch.Tensor, z_test: Optional[torch.Tensor],
+                 stream=None):
+    s = plan.sizes
+    _check(lib().bs_beamspace(plan.handle, _ptr(xc, torch.complex64, s.xc_elems, "xc"),
+                              _ztr_check(plan, z_train),
+                              _ptr(z_test, torch.complex64, s.ztest_elems, "z_test"),
+                              _stream(stream)), "bs_beamspace")
+
+
+def bs_beamspace_full(plan: Plan, y: torch.Tensor, yb: torch.Tensor, nvec: int, stream=None):
+    _check(lib().bs_beamspace_full(plan.handle, _ptr(y, torch.complex64, nvec * plan.N, "y"), nvec,
+                                   _ptr(yb, torch.complex64, nvec * plan.M, "yb"), _stream(stream)),
+           "bs_beamspace_full")
+
+
+def bs_window_cov(plan: Plan, z_train: torch.Tensor, R: torch.Tensor,
+                  delta_pair: Optional[torch.Tensor] = None, stream=None):
+    s = plan.sizes
+    _check(lib().bs_window_cov(plan.handle, _ztr_check(plan, z_train),
+                               _ptr(delta_pair, torch.float32, s.pairs, "delta_pair"),
+                               _ptr(R, torch.complex128, s.r_elems, "R"), _stream(stream)),
+           "bs_window_cov")
+
+
+def bs_mvdr_solve(plan: Plan, R: torch.Tensor, c: torch.Tensor, info: torch.Tensor, stream=None):
+    s = plan.sizes
+    _check(lib().bs_mvdr_solve(plan.handle, _ptr(R, torch.complex128, s.r_elems, "R"),
+                               _ptr(c, torch.complex64, s.c_elems, "c"),
+                               _ptr(info, torch.int32, s.pairs, "info"), _stream(stream)),
+           "bs_mvdr_solve")
+
+
+def bs_apply(plan: Plan, z_test: torch.Tensor, c: torch.Tensor, out: torch.Tensor, stream=None):
+    s = plan.sizes
+    _check(lib().bs_apply(plan.handle, _ptr(z_test, torch.complex64, s.ztest_elems, "z_test"),
+                          _ptr(c, torch.complex64, s.c_elems, "c"),
+                          _ptr(out, torch.complex64, s.out_elems, "out"), _stream(stream)), "bs_apply")
+
+
+def _cbuf(plan: Plan, b: Buffers) -> _Buffers:
+    s = plan.sizes
+    return _Buffers(_ptr(b.x, torch.complex64, s.x_elems, "x"),
+                    _ptr(b.xc, torch.complex64, s.xc_elems, "xc"),
+                    _ztr_check(plan, b.z_train),
+                    _ptr(b.z_test, torch.complex64, s.ztest_elems, "z_test"),
+                    _ptr(b.R, torch.complex128, s.r_elems, "R"),
+                    _ptr(b.c, torch.complex64, s.c_elems, "c"),
+                    _ptr(b.info, torch.int32, s.pairs, "info"),
+                    _ptr(b.out, torch.complex64, s.out_elems, "out"))
+
+
+def bs_run(plan: Plan, bufs: Buffers, stream=None):
+    cb = _cbuf(plan, bufs)
+    _check(lib().bs_run(plan.handle, ctypes.byref(cb), _stream(stream)), "bs_run")
+
+
+def bs_run_host(plan: Plan, x_host: torch.Tensor, out_host: torch.Tensor, bufs: Buffers, stream=None):
+    s = plan.sizes
+    for t, n, name in ((x_host, s.x_elems, "x_host"), (out_host, s.out_elems, "out_host")):
+        if t.is_cuda or not t.is_contiguous() or t.dtype != torch.complex64 or t.numel() < n:
+            raise BsError(f"{name} must be a contiguous complex64 host tensor of >= {n} elements")
+    cb = _cbuf(plan, bufs)
+    _check(lib().bs_run_host(plan.handle, x_host.data_ptr(), out_host.data_ptr(), ctypes.byref(cb),
+                             _stream(stream)), "bs_run_host")

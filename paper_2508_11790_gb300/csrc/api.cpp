@@ -1,0 +1,102 @@
+// extern "C" entry points of the hot path: argument checks, then the
+// kernel launchers of the individual translation units.
+#include <string>
+
+#include "internal.h"
+
+using bs::set_error;
+
+static bs_status check_device(const bs_plan *p) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return bs::cuda_error(e, "cudaGetDevice");
+    if (dev != p->device) return set_error(BS_EINVAL, "current device differs from the plan's device");
+    return BS_OK;
+}
+
+#define BS_REQUIRE(cond, msg)                                  \
+    do {                                                       \
+        if (!(cond)) return set_error(BS_EINVAL, (msg));       \
+    } while (0)
+
+extern "C" {
+
+bs_status bs_channelize(const bs_plan *p, const bs_cf32 *x, int32_t P, bs_cf32 *xc, bs_stream stream) {
+    BS_REQUIRE(p, "NULL plan");
+    BS_REQUIRE(P >= 0, "P must be >= 0");
+    if (P == 0) return BS_OK;
+    BS_REQUIRE(x && xc, "NULL buffer");
+    BS_REQUIRE((const void *)x != (const void *)xc, "x and xc must be distinct");
+    BS_REQUIRE(P <= 65535, "at most 65535 records per call");
+    if (bs_status s = check_device(p)) return s;
+    return bs::launch_channelize(p, (const float2 *)x, P, (float2 *)xc, (cudaStream_t)stream);
+}
+
+bs_status bs_beamspace(const bs_plan *p, const bs_cf32 *xc, void *z_train, bs_cf32 *z_test, bs_stream stream) {
+    BS_REQUIRE(p, "NULL plan");
+    BS_REQUIRE(xc && z_train, "NULL buffer");
+    BS_REQUIRE(z_test || p->cfg.P_test == 0, "z_test is NULL but P_test > 0");
+    if (bs_status s = check_device(p)) return s;
+    return bs::launch_beamspace(p, (const float2 *)xc, z_train, (float2 *)z_test, (cudaStream_t)stream);
+}
+
+bs_status bs_beamspace_full(const bs_plan *p, const bs_cf32 *y, int64_t nvec, bs_cf32 *yb, bs_stream stream) {
+    BS_REQUIRE(p, "NULL plan");
+    BS_REQUIRE(nvec >= 0, "nvec must be >= 0");
+    if (nvec == 0) return BS_OK;
+    BS_REQUIRE(y && yb, "NULL buffer");
+    if (bs_status s = check_device(p)) return s;
+    return bs::launch_beamspace_full(p, (const float2 *)y, nvec, (float2 *)yb, (cudaStream_t)stream);
+}
+
+bs_status bs_window_cov(const bs_plan *p, const void *z_train, const float *delta_pair, bs_cf64 *R,
+                        bs_stream stream) {
+    BS_REQUIRE(p, "NULL plan");
+    BS_REQUIRE(z_train && R, "NULL buffer");
+    if (bs_status s = check_device(p)) return s;
+    return bs::launch_window_cov(p, z_train, delta_pair, (double2 *)R, (cudaStream_t)stream);
+}
+
+bs_status bs_mvdr_solve(const bs_plan *p, const bs_cf64 *R, bs_cf32 *c, int32_t *info, bs_stream stream) {
+    BS_REQUIRE(p, "NULL plan");
+    BS_REQUIRE(R && c && info, "NULL buffer");
+    if (bs_status s = check_device(p)) return s;
+    return bs::launch_mvdr_solve(p, (const double2 *)R, (float2 *)c, info, (cudaStream_t)stream);
+}
+
+bs_status bs_apply(const bs_plan *p, const bs_cf32 *z_test, const bs_cf32 *c, bs_cf32 *out, bs_stream stream) {
+    BS_REQUIRE(p, "NULL plan");
+    if (p->Vte == 0) return BS_OK;
+    BS_REQUIRE(z_test && c && out, "NULL buffer");
+    if (bs_status s = check_device(p)) return s;
+    return bs::launch_apply(p, (const float2 *)z_test, (const float2 *)c, (float2 *)out, (cudaStream_t)stream);
+}
+
+bs_status bs_run(const bs_plan *p, const bs_buffers *b, bs_stream stream) {
+    BS_REQUIRE(p && b, "NULL argument");
+    bs_status s;
+    if ((s = bs_channelize(p, b->x, p->P, b->xc, stream))) return s;
+    if ((s = bs_beamspace(p, b->xc, b->z_train, b->z_test, stream))) return s;
+    if ((s = bs_window_cov(p, b->z_train, nullptr, b->R, stream))) return s;
+    if ((s = bs_mvdr_solve(p, b->R, b->c, b->info, stream))) return s;
+    return bs_apply(p, b->z_test, b->c, b->out, stream);
+}
+
+bs_status bs_run_host(const bs_plan *p, const bs_cf32 *x_host, bs_cf32 *out_host, const bs_buffers *b,
+                      bs_stream stream) {
+    BS_REQUIRE(p && b && x_host && out_host, "NULL argument");
+    BS_REQUIRE(b->x && b->out, "buf->x and buf->out must be device buffers");
+    const cudaStream_t st = (cudaStream_t)stream;
+    const size_t xbytes = (size_t)p->P * p->cfg.F * p->cfg.N * sizeof(bs_cf32);
+    const size_t obytes = (size_t)p->pairs * p->Vte * sizeof(bs_cf32);
+    cudaError_t e = cudaMemcpyAsync((void *)b->x, x_host, xbytes, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return bs::cuda_error(e, "host to device copy");
+    if (bs_status s = bs_run(p, b, stream)) return s;
+    if (obytes) {
+        e = cudaMemcpyAsync(out_host, b->out, obytes, cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) return bs::cuda_error(e, "device to host copy");
+    }
+    return bs::cuda_error(cudaStreamSynchronize(st), "stream synchronise");
+}
+
+}  // extern "C"

@@ -1,0 +1,189 @@
+// Beamspace transform and window gather (Eq. VerDFT, Eq. BeamTransform,
+// Eq. OverallWindow, Eq. ApplyWindow).
+//
+// Every (record, bin) vector of N elements (contiguous in the channelised
+// cube) is zero-padded to M points and transformed by an M-point Stockham
+// FFT in shared memory; a CTA takes VPB consecutive vectors.  The windowed
+// variant then writes, for every target, the W_t beams of its window
+// (start_g + w mod M) straight from shared memory into the packed training
+// or test window arrays; the full variant writes all M beams.
+#include "common.cuh"
+#include "internal.h"
+
+namespace bs {
+
+template <int M>
+struct BsCfg {
+    static constexpr int vpb = (8192 / M > 16) ? 16 : ((8192 / M < 1) ? 1 : 8192 / M);
+    static constexpr int nthr = (vpb * M / 16 < 256) ? vpb * M / 16 : 256;
+    static constexpr int pl = padded_len(M);
+    static constexpr size_t smem = (size_t)vpb * pl * sizeof(float2);
+};
+
+struct GatherArgs {
+    int64_t nvec;           // vectors = P * F
+    int log2F, log2B, L, P_train;
+    const int32_t *gather;  // [vpb * sumW] (t << 16) | k
+    int ngather;
+    const int32_t *Wg, *Kg, *start;
+    const int64_t *ztr_off, *zte_off;
+    void *ztr;              // training windows (plan precision)
+    float2 *zte;            // test windows
+    float store_scale;
+};
+
+template <int PREC>
+__device__ __forceinline__ void store_train(void *z, int64_t idx, float2 v, float sc) {
+    if constexpr (PREC == BS_PREC_FP32) {
+        reinterpret_cast<float2 *>(z)[idx] = v;
+    } else if constexpr (PREC == BS_PREC_FP16) {
+        reinterpret_cast<__half2 *>(z)[idx] = __floats2half2_rn(v.x * sc, v.y * sc);
+    } else {
+        reinterpret_cast<__nv_bfloat162 *>(z)[idx] = __floats2bfloat162_rn(v.x * sc, v.y * sc);
+    }
+}
+
+// kFull: write all M beams to out[v][m]; else gather windows (PREC = storage
+// precision of the training windows).
+template <int M, bool kFull, int PREC>
+__global__ void __launch_bounds__(BsCfg<M>::nthr)
+    beamspace_kernel(const float2 *__restrict__ y, int64_t nvec, int N, const float2 *__restrict__ tw,
+                     float scale, float2 *__restrict__ out, GatherArgs ga) {
+    using RP = Radix<M>;
+    constexpr int vpb = BsCfg<M>::vpb;
+    constexpr int nthr = BsCfg<M>::nthr;
+    constexpr int pl = BsCfg<M>::pl;
+    extern __shared__ float2 sm[];
+    const int tid = threadIdx.x;
+    const int64_t vid0 = (int64_t)blockIdx.x * vpb;
+
+    auto gload = [&](int c, int n) -> float2 {
+        const int64_t v = vid0 + c;
+        if (n >= N || v >= nvec) return make_float2(0.f, 0.f);
+        return __ldcs(&y[v * N + n]);
+    };
+    auto sload = [&](int c, int m) -> float2 { return sm[c * pl + padrow(m)]; };
+    auto sstore = [&](int c, int m, float2 v) { sm[c * pl + padrow(m)] = v; };
+
+    if constexpr (RP::npass == 1) {
+        stockham_pass<M, RP::r0, 1, vpb, nthr, false, false>(tid, tw, gload, sstore);
+    } else if constexpr (RP::npass == 2) {
+        stockham_pass<M, RP::r0, 1, vpb, nthr, false, false>(tid, tw, gload, sstore);
+        __syncthreads();
+        stockham_pass<M, RP::r1, RP::r0, vpb, nthr, false, true>(tid, tw, sload, sstore);
+    } else {
+        stockham_pass<M, RP::r0, 1, vpb, nthr, false, false>(tid, tw, gload, sstore);
+        __syncthreads();
+        stockham_pass<M, RP::r1, RP::r0, vpb, nthr, false, true>(tid, tw, sload, sstore);
+        __syncthreads();
+        stockham_pass<M, RP::r2, RP::r0 * RP::r1, vpb, nthr, false, true>(tid, tw, sload, sstore);
+    }
+    __syncthreads();
+
+    if constexpr (kFull) {
+        for (int e = tid; e < vpb * M; e += nthr) {
+            const int c = e / M, m = e % M;
+            const int64_t v = vid0 + c;
+            if (v < nvec) out[v * M + m] = cscale(sload(c, m), scale);
+        }
+    } else {
+        const int Fm1 = (1 << ga.log2F) - 1, Bm1 = (1 << ga.log2B) - 1;
+        for (int e = tid; e < ga.ngather; e += nthr) {
+            const int packed = __ldg(&ga.gather[e]);
+            const int t = packed >> 16, k = packed & 0xFFFF;
+            const int64_t g0 = (int64_t)t * ga.L;
+            const int W = __ldg(&ga.Wg[g0]);
+            const int c = k / W, w = k - c * W;
+            const int64_t vid = vid0 + c;
+            if (vid >= nvec) continue;
+            const int p = (int)(vid >> ga.log2F);
+            const int q = (int)(vid & Fm1);
+            const int s = q >> ga.log2B, i = q & Bm1;
+            const int64_t g = g0 + s;
+            const int m = (__ldg(&ga.start[g]) + w) & (M - 1);
+            const float2 val = cscale(sload(c, m), scale);
+            if (p < ga.P_train) {
+                const int vv = (p << ga.log2B) + i;
+                if (vv < __ldg(&ga.Kg[g]))
+                    store_train<PREC>(ga.ztr, __ldg(&ga.ztr_off[g]) + (int64_t)vv * W + w, val, ga.store_scale);
+            } else {
+                const int vv = ((p - ga.P_train) << ga.log2B) + i;
+                ga.zte[__ldg(&ga.zte_off[g]) + (int64_t)vv * W + w] = val;
+            }
+        }
+    }
+}
+
+template <int M, bool kFull, int PREC>
+static bs_status launch_bs_t(const float2 *y, int64_t nvec, int N, const float2 *tw, float2 *out,
+                             const GatherArgs &ga, cudaStream_t st) {
+    using C = BsCfg<M>;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(beamspace_kernel<M, kFull, PREC>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem);
+        if (e != cudaSuccess) return cuda_error(e, "beamspace attribute");
+        attr_set = true;
+    }
+    const int64_t blocks = (nvec + C::vpb - 1) / C::vpb;
+    if (blocks > 0x7FFFFFFF) return set_error(BS_EUNSUPPORTED, "too many vectors");
+    if (blocks == 0) return BS_OK;
+    beamspace_kernel<M, kFull, PREC><<<(unsigned)blocks, C::nthr, C::smem, st>>>(
+        y, nvec, N, tw, 1.0f / sqrtf((float)M), out, ga);
+    return check_launch("beamspace launch");
+}
+
+template <bool kFull, int PREC>
+static bs_status launch_bs(int M, const float2 *y, int64_t nvec, int N, const float2 *tw, float2 *out,
+                           const GatherArgs &ga, cudaStream_t st) {
+    switch (M) {
+        case 16: return launch_bs_t<16, kFull, PREC>(y, nvec, N, tw, out, ga, st);
+        case 32: return launch_bs_t<32, kFull, PREC>(y, nvec, N, tw, out, ga, st);
+        case 64: return launch_bs_t<64, kFull, PREC>(y, nvec, N, tw, out, ga, st);
+        case 128: return launch_bs_t<128, kFull, PREC>(y, nvec, N, tw, out, ga, st);
+        case 256: return launch_bs_t<256, kFull, PREC>(y, nvec, N, tw, out, ga, st);
+        case 512: return launch_bs_t<512, kFull, PREC>(y, nvec, N, tw, out, ga, st);
+        case 1024: return launch_bs_t<1024, kFull, PREC>(y, nvec, N, tw, out, ga, st);
+        case 2048: return launch_bs_t<2048, kFull, PREC>(y, nvec, N, tw, out, ga, st);
+        case 4096: return launch_bs_t<4096, kFull, PREC>(y, nvec, N, tw, out, ga, st);
+    }
+    return set_error(BS_EUNSUPPORTED, "M not supported");
+}
+
+static int ilog2(int v) {
+    int r = 0;
+    while ((1 << r) < v) ++r;
+    return r;
+}
+
+bs_status launch_beamspace(const bs_plan *p, const float2 *xc, void *ztr, float2 *zte, cudaStream_t st) {
+    GatherArgs ga;
+    ga.nvec = (int64_t)p->P * p->cfg.F;
+    ga.log2F = ilog2(p->cfg.F);
+    ga.log2B = ilog2(p->B);
+    ga.L = p->cfg.L;
+    ga.P_train = p->cfg.P_train;
+    ga.gather = p->d_gather;
+    ga.ngather = (int)p->gather.size();
+    ga.Wg = p->d_Wg;
+    ga.Kg = p->d_Kg;
+    ga.start = p->d_start;
+    ga.ztr_off = p->d_ztr_off;
+    ga.zte_off = p->d_zte_off;
+    ga.ztr = ztr;
+    ga.zte = zte;
+    ga.store_scale = p->cfg.store_scale;
+    switch (p->cfg.precision) {
+        case BS_PREC_FP32: return launch_bs<false, BS_PREC_FP32>(p->cfg.M, xc, ga.nvec, p->cfg.N, p->d_twM, nullptr, ga, st);
+        case BS_PREC_FP16: return launch_bs<false, BS_PREC_FP16>(p->cfg.M, xc, ga.nvec, p->cfg.N, p->d_twM, nullptr, ga, st);
+        default: return launch_bs<false, BS_PREC_BF16>(p->cfg.M, xc, ga.nvec, p->cfg.N, p->d_twM, nullptr, ga, st);
+    }
+}
+
+bs_status launch_beamspace_full(const bs_plan *p, const float2 *y, int64_t nvec, float2 *yb,
+                                cudaStream_t st) {
+    GatherArgs ga{};
+    return launch_bs<true, BS_PREC_FP32>(p->cfg.M, y, nvec, p->cfg.N, p->d_twM, yb, ga, st);
+}
+
+}  // namespace bs

@@ -1,0 +1,54 @@
+// Plan object and launch helpers shared by the translation units of the
+// library (host side).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "bs.h"
+
+struct bs_plan {
+    bs_config cfg;              // host pointers cleared after create
+    int B = 0, P = 0, Vte = 0, Wmax = 0, Kmax = 0, sumW = 0;
+    int64_t pairs = 0;
+    std::vector<int32_t> Wt, Kt;        // per target
+    std::vector<double> u;              // per target
+    // per pair (g = t * L + s)
+    std::vector<int32_t> start, Wg, Kg;
+    std::vector<int64_t> woff, ztr_off, zte_off, roff;   // pairs + 1 entries
+    std::vector<bs_cf64> at;                              // windowed steering, woff-packed
+    int64_t ztr_elems = 0, zte_elems = 0, r_elems = 0, c_elems = 0;
+    // beamspace gather: vectors per CTA and the (target, k) table of one CTA
+    int vpb = 0;
+    std::vector<int32_t> gather;        // [vpb * sumW]: (t << 16) | k, k = c * W_t + w
+    // device copies
+    int device = 0;
+    int32_t *d_start = nullptr, *d_Wg = nullptr, *d_Kg = nullptr, *d_gather = nullptr;
+    int64_t *d_woff = nullptr, *d_ztr_off = nullptr, *d_zte_off = nullptr, *d_roff = nullptr;
+    float2 *d_at32 = nullptr;
+    double2 *d_at64 = nullptr;
+    float2 *d_twF = nullptr, *d_twM = nullptr;   // e^{-2 pi i k / F}, e^{-2 pi i k / M}
+};
+
+namespace bs {
+
+bs_status set_error(bs_status s, const std::string &msg);
+bs_status cuda_error(cudaError_t e, const char *where);
+bs_status check_launch(const char *where);
+
+// kernel launchers (one per translation unit)
+bs_status launch_channelize(const bs_plan *p, const float2 *x, int P, float2 *xc, cudaStream_t st);
+bs_status launch_beamspace(const bs_plan *p, const float2 *xc, void *ztr, float2 *zte, cudaStream_t st);
+bs_status launch_beamspace_full(const bs_plan *p, const float2 *y, int64_t nvec, float2 *yb,
+                                cudaStream_t st);
+bs_status launch_window_cov(const bs_plan *p, const void *ztr, const float *delta, double2 *R,
+                            cudaStream_t st);
+bs_status launch_mvdr_solve(const bs_plan *p, const double2 *R, float2 *c, int32_t *info,
+                            cudaStream_t st);
+bs_status launch_apply(const bs_plan *p, const float2 *zte, const float2 *c, float2 *out,
+                       cudaStream_t st);
+int beamspace_vectors_per_cta(int M);
+
+}  // namespace bs
