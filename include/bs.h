@@ -73,6 +73,7 @@ typedef enum {
                                         FP32 sums, FP32 Cholesky, no refinement */
 #define BS_FLAG_NO_REFINE  (1u << 1) /* skip the iterative-refinement step */
 #define BS_FLAG_NO_FP64    (1u << 2) /* never escalate a pair to the FP64 solve */
+#define BS_FLAG_NO_TMA     (1u << 3) /* channeliser without the TMA-staged persistent kernel */
 
 typedef struct { float re, im; } bs_cf32;
 typedef struct { double re, im; } bs_cf64;
@@ -156,6 +157,12 @@ bs_status bs_plan_offsets(const bs_plan *plan, int32_t *start, int32_t *W, int32
  * windowed steering vectors (pair order, W_g values each).  Either output
  * may be NULL.  Errors: as bs_plan_create's argument checks. */
 bs_status bs_plan_tables_host(const bs_config *cfg, int32_t *start, bs_cf64 *a_tilde);
+
+/* Synchronises the device and reads the plan's device error word, which a
+ * kernel sets when one of its bounded waits (TMA / mbarrier) gives up.
+ * flags (may be NULL) receives the word; it is cleared after reading.
+ * Returns BS_ETIMEOUT if it was set, else BS_OK. */
+bs_status bs_plan_device_status(const bs_plan *plan, int32_t *flags);
 
 /* ----------------------------------------------------------- hot path --- */
 

@@ -19,14 +19,14 @@ from .build import lib_path
 
 __all__ = [
     "BS_PREC_FP32", "BS_PREC_FP16", "BS_PREC_BF16",
-    "BS_FLAG_PLAIN", "BS_FLAG_NO_REFINE", "BS_FLAG_NO_FP64",
+    "BS_FLAG_PLAIN", "BS_FLAG_NO_REFINE", "BS_FLAG_NO_FP64", "BS_FLAG_NO_TMA",
     "BsError", "Plan", "Buffers", "alloc_buffers", "lib", "bs_plan_tables_host",
     "bs_channelize", "bs_beamspace", "bs_beamspace_full", "bs_window_cov",
     "bs_mvdr_solve", "bs_apply", "bs_run", "bs_run_host",
 ]
 
 BS_PREC_FP32, BS_PREC_FP16, BS_PREC_BF16 = 0, 1, 2
-BS_FLAG_PLAIN, BS_FLAG_NO_REFINE, BS_FLAG_NO_FP64 = 1, 2, 4
+BS_FLAG_PLAIN, BS_FLAG_NO_REFINE, BS_FLAG_NO_FP64, BS_FLAG_NO_TMA = 1, 2, 4, 8
 
 
 class BsError(RuntimeError):
@@ -74,6 +74,7 @@ _SIGS = {
     "bs_run": ([_P, ctypes.POINTER(_Buffers), _P], ctypes.c_int),
     "bs_run_host": ([_P, _P, _P, ctypes.POINTER(_Buffers), _P], ctypes.c_int),
     "bs_plan_tables_host": ([ctypes.POINTER(_Config), _P, _P], ctypes.c_int),
+    "bs_plan_device_status": ([_P, _P], ctypes.c_int),
     "bs_status_string": ([ctypes.c_int], ctypes.c_char_p),
     "bs_last_error": ([], ctypes.c_char_p),
 }
@@ -215,6 +216,14 @@ class Plan:
         args = [out[k].ctypes.data for k in ("start", "W", "K", "woff", "ztr_off", "zte_off", "roff", "a_tilde")]
         _check(lib().bs_plan_offsets(self._h, *args), "bs_plan_offsets")
         return out
+
+    def device_status(self) -> int:
+        """Synchronise, return and clear the device error word (raises on a
+        bounded-wait timeout)."""
+        flags = ctypes.c_int32(0)
+        st = lib().bs_plan_device_status(self._h, ctypes.byref(flags))
+        _check(st, "bs_plan_device_status")
+        return flags.value
 
     def close(self) -> None:
         if getattr(self, "_h", None):

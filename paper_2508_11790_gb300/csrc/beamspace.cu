@@ -12,18 +12,23 @@
 
 namespace bs {
 
+// Vectors per CTA: vpb = 4096 / M clamped to [1, 16] (34.8 KB of padded
+// shared memory at M = 2048), 256 threads, one radix-16 butterfly per thread
+// per pass, so that four CTAs (32 warps) share an SM.
 template <int M>
 struct BsCfg {
-    static constexpr int vpb = (8192 / M > 16) ? 16 : ((8192 / M < 1) ? 1 : 8192 / M);
+    static constexpr int vpb = (4096 / M > 16) ? 16 : ((4096 / M < 1) ? 1 : 4096 / M);
     static constexpr int nthr = (vpb * M / 16 < 256) ? vpb * M / 16 : 256;
     static constexpr int pl = padded_len(M);
     static constexpr size_t smem = (size_t)vpb * pl * sizeof(float2);
+    static constexpr int minb = (smem <= 40 * 1024) ? 4 : ((smem <= 72 * 1024) ? 3 : 1);
 };
 
 struct GatherArgs {
     int64_t nvec;           // vectors = P * F
-    int log2F, log2B, L, P_train;
-    const int32_t *gather;  // [vpb * sumW] (t << 16) | k
+    int log2F, log2B, L, P_train, T;
+    int uniform;            // B % vpb == 0: the vectors of a CTA share (record, subband)
+    const int32_t *gather;  // [vpb * sumW] (t << 8) | (c << 4) | w
     int ngather;
     const int32_t *Wg, *Kg, *start;
     const int64_t *ztr_off, *zte_off;
@@ -43,10 +48,35 @@ __device__ __forceinline__ void store_train(void *z, int64_t idx, float2 v, floa
     }
 }
 
+constexpr int kTabT = 256;   // targets whose gather entries are staged in shared memory
+
+// Gather entry of target t for a CTA at subband s whose first vector is v0:
+// base element offset in the window array, start | (W << 16), output count.
+__device__ __forceinline__ void fill_target_entry(const GatherArgs &ga, int t, int s, int v0, int nv,
+                                                  bool train, long long *base, int *sw, int *nout,
+                                                  int slot = -1) {
+    const int i = slot < 0 ? t : slot;
+    const int64_t g = (int64_t)t * ga.L + s;
+    const int W = __ldg(&ga.Wg[g]);
+    const int st = __ldg(&ga.start[g]);
+    int n = nv * W;
+    long long b;
+    if (train) {
+        const int K = __ldg(&ga.Kg[g]);
+        n = (v0 >= K) ? 0 : min(n, (K - v0) * W);
+        b = __ldg(&ga.ztr_off[g]) + (long long)v0 * W;
+    } else {
+        b = __ldg(&ga.zte_off[g]) + (long long)v0 * W;
+    }
+    base[i] = b;
+    sw[i] = st | (W << 16);
+    nout[i] = n;
+}
+
 // kFull: write all M beams to out[v][m]; else gather windows (PREC = storage
 // precision of the training windows).
 template <int M, bool kFull, int PREC>
-__global__ void __launch_bounds__(BsCfg<M>::nthr)
+__global__ void __launch_bounds__(BsCfg<M>::nthr, BsCfg<M>::minb)
     beamspace_kernel(const float2 *__restrict__ y, int64_t nvec, int N, const float2 *__restrict__ tw,
                      float scale, float2 *__restrict__ out, GatherArgs ga) {
     using RP = Radix<M>;
@@ -54,8 +84,28 @@ __global__ void __launch_bounds__(BsCfg<M>::nthr)
     constexpr int nthr = BsCfg<M>::nthr;
     constexpr int pl = BsCfg<M>::pl;
     extern __shared__ float2 sm[];
+    // per-target gather entries of this CTA (uniform path), filled before the
+    // FFT so that the table loads overlap the butterflies
+    __shared__ long long tab_base[kTabT];
+    __shared__ int tab_sw[kTabT];     // start | (W << 16)
+    __shared__ int tab_n[kTabT];      // outputs of this target in this CTA (0: none)
     const int tid = threadIdx.x;
     const int64_t vid0 = (int64_t)blockIdx.x * vpb;
+    int s_cta = 0, v0_cta = 0;
+    bool train_cta = false;
+    if constexpr (!kFull) {
+        if (ga.uniform && vid0 < ga.nvec) {
+            const int p = (int)(vid0 >> ga.log2F);
+            const int q = (int)(vid0 & ((1 << ga.log2F) - 1));
+            s_cta = q >> ga.log2B;
+            const int i0 = q & ((1 << ga.log2B) - 1);
+            train_cta = p < ga.P_train;
+            v0_cta = train_cta ? (p << ga.log2B) + i0 : ((p - ga.P_train) << ga.log2B) + i0;
+            const int nv = (ga.nvec - vid0 < (int64_t)vpb) ? (int)(ga.nvec - vid0) : vpb;
+            for (int t = tid; t < ga.T && t < kTabT; t += nthr)
+                fill_target_entry(ga, t, s_cta, v0_cta, nv, train_cta, tab_base, tab_sw, tab_n);
+        }
+    }
 
     auto gload = [&](int c, int n) -> float2 {
         const int64_t v = vid0 + c;
@@ -86,14 +136,39 @@ __global__ void __launch_bounds__(BsCfg<M>::nthr)
             const int64_t v = vid0 + c;
             if (v < nvec) out[v * M + m] = cscale(sload(c, m), scale);
         }
+    } else if (ga.uniform) {
+        // All vpb vectors share record p and subband s (bins i0 .. i0+vpb-1).
+        // Flat loop over the (target, vector c, beam w) entries of the gather
+        // table; the vpb * W_t outputs of target t form one contiguous run of
+        // the window array (element k = c * W_t + w from the target's base).
+        if (vid0 >= ga.nvec) return;
+        const int nv = (ga.nvec - vid0 < (int64_t)vpb) ? (int)(ga.nvec - vid0) : vpb;
+        for (int e = tid; e < ga.ngather; e += nthr) {
+            const int packed = __ldg(&ga.gather[e]);
+            const int t = packed >> 8, c = (packed >> 4) & 15, w = packed & 15;
+            long long base;
+            int sw, nout;
+            if (t < kTabT) {
+                base = tab_base[t];
+                sw = tab_sw[t];
+                nout = tab_n[t];
+            } else {
+                fill_target_entry(ga, t, s_cta, v0_cta, nv, train_cta, &base, &sw, &nout, 0);
+            }
+            const int W = sw >> 16;
+            const int k = c * W + w;
+            if (k >= nout) continue;
+            const float2 val = cscale(sload(c, ((sw & 0xFFFF) + w) & (M - 1)), scale);
+            if (train_cta) store_train<PREC>(ga.ztr, base + k, val, ga.store_scale);
+            else ga.zte[base + k] = val;
+        }
     } else {
         const int Fm1 = (1 << ga.log2F) - 1, Bm1 = (1 << ga.log2B) - 1;
         for (int e = tid; e < ga.ngather; e += nthr) {
             const int packed = __ldg(&ga.gather[e]);
-            const int t = packed >> 16, k = packed & 0xFFFF;
+            const int t = packed >> 8, c = (packed >> 4) & 15, w = packed & 15;
             const int64_t g0 = (int64_t)t * ga.L;
             const int W = __ldg(&ga.Wg[g0]);
-            const int c = k / W, w = k - c * W;
             const int64_t vid = vid0 + c;
             if (vid >= nvec) continue;
             const int p = (int)(vid >> ga.log2F);
@@ -162,7 +237,9 @@ bs_status launch_beamspace(const bs_plan *p, const float2 *xc, void *ztr, float2
     ga.log2F = ilog2(p->cfg.F);
     ga.log2B = ilog2(p->B);
     ga.L = p->cfg.L;
+    ga.T = p->cfg.T;
     ga.P_train = p->cfg.P_train;
+    ga.uniform = (p->B % p->vpb) == 0;
     ga.gather = p->d_gather;
     ga.ngather = (int)p->gather.size();
     ga.Wg = p->d_Wg;

@@ -84,6 +84,34 @@ struct Radix {
     static_assert(n >= 2 && n <= 4096 && (n & (n - 1)) == 0, "n must be a power of two <= 4096");
 };
 
+// w[r] = tw[r * e] for r < R (R = 2, 4, 8, 16; r * e < table length).
+// Only w^1, w^4, w^8 and w^12 come from the table; the other powers are
+// products of at most three table entries, which keeps their error within
+// a few FP32 ulps while cutting the table loads per butterfly from R-1 to
+// at most 4 (the loads of a warp hit scattered table lines).
+template <int R>
+__device__ __forceinline__ void twiddle_powers(const float2 *__restrict__ tw, int e, float2 (&w)[R]) {
+    w[0] = make_float2(1.f, 0.f);
+    w[1] = __ldg(&tw[e]);
+    if constexpr (R >= 4) {
+        w[2] = cmul(w[1], w[1]);
+        w[3] = cmul(w[2], w[1]);
+    }
+    if constexpr (R >= 8) {
+        w[4] = __ldg(&tw[4 * e]);
+#pragma unroll
+        for (int r = 5; r < 8; ++r) w[r] = cmul(w[4], w[r - 4]);
+    }
+    if constexpr (R >= 16) {
+        w[8] = __ldg(&tw[8 * e]);
+        w[12] = __ldg(&tw[12 * e]);
+#pragma unroll
+        for (int r = 9; r < 12; ++r) w[r] = cmul(w[8], w[r - 8]);
+#pragma unroll
+        for (int r = 13; r < 16; ++r) w[r] = cmul(w[12], w[r - 12]);
+    }
+}
+
 // One Stockham autosort pass (decimation in time) of an n-point FFT over a
 // batch of `ncols` independent columns, processed by `nthr` threads:
 //   butterfly j < n/R of column c reads a[j + r n/R] (r < R), multiplies
@@ -111,9 +139,10 @@ __device__ __forceinline__ void stockham_pass(int tid, const float2 *__restrict_
 #pragma unroll
         for (int r = 0; r < R; ++r) v[b][r] = load(c, j + r * (n / R));
         if (Ns > 1) {
-            const int k = j % Ns;
+            float2 w[R];
+            twiddle_powers<R>(tw, (j % Ns) * (n / (Ns * R)), w);
 #pragma unroll
-            for (int r = 1; r < R; ++r) v[b][r] = cmul(v[b][r], __ldg(&tw[r * k * (n / (Ns * R))]));
+            for (int r = 1; r < R; ++r) v[b][r] = cmul(v[b][r], w[r]);
         }
         RegDFT<R>::run(v[b]);
     }

@@ -22,7 +22,7 @@ struct bs_plan {
     int64_t ztr_elems = 0, zte_elems = 0, r_elems = 0, c_elems = 0;
     // beamspace gather: vectors per CTA and the (target, k) table of one CTA
     int vpb = 0;
-    std::vector<int32_t> gather;        // [vpb * sumW]: (t << 16) | k, k = c * W_t + w
+    std::vector<int32_t> gather;        // [vpb * sumW]: (t << 8) | (c << 4) | w, target-major
     // device copies
     int device = 0;
     int32_t *d_start = nullptr, *d_Wg = nullptr, *d_Kg = nullptr, *d_gather = nullptr;
@@ -30,6 +30,8 @@ struct bs_plan {
     float2 *d_at32 = nullptr;
     double2 *d_at64 = nullptr;
     float2 *d_twF = nullptr, *d_twM = nullptr;   // e^{-2 pi i k / F}, e^{-2 pi i k / M}
+    int *d_err = nullptr;                        // device error word (bit 0: a bounded wait gave up)
+    int num_sms = 0;
 };
 
 namespace bs {

@@ -27,7 +27,7 @@ bs_status cuda_error(cudaError_t e, const char *where) {
 bs_status check_launch(const char *where) { return cuda_error(cudaGetLastError(), where); }
 
 int beamspace_vectors_per_cta(int M) {
-    int v = 8192 / M;
+    int v = 4096 / M;
     if (v < 1) v = 1;
     if (v > 16) v = 16;
     return v;
@@ -123,6 +123,7 @@ void bs_plan_destroy(bs_plan *p) {
     cudaFree(p->d_at64);
     cudaFree(p->d_twF);
     cudaFree(p->d_twM);
+    cudaFree(p->d_err);
     delete p;
 }
 
@@ -244,7 +245,8 @@ bs_status bs_plan_create(bs_plan **out, const bs_config *cfg) {
     p->vpb = bs::beamspace_vectors_per_cta(c.M);
     p->gather.reserve((size_t)p->vpb * p->sumW);
     for (int t = 0; t < c.T; ++t)
-        for (int k = 0; k < p->vpb * p->Wt[t]; ++k) p->gather.push_back((t << 16) | k);
+        for (int cc = 0; cc < p->vpb; ++cc)
+            for (int w = 0; w < p->Wt[t]; ++w) p->gather.push_back((t << 8) | (cc << 4) | w);
 
     cudaGetDevice(&p->device);
     bs_status st = BS_OK;
@@ -260,11 +262,29 @@ bs_status bs_plan_create(bs_plan **out, const bs_config *cfg) {
     if (!st) st = upload(&p->d_at64, at64);
     if (!st) st = upload(&p->d_twF, twiddles(c.F));
     if (!st) st = upload(&p->d_twM, twiddles(c.M));
+    if (!st) st = upload(&p->d_err, std::vector<int>(1, 0));
+    if (!st) st = bs::cuda_error(cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device),
+                                 "device attribute");
     if (st) {
         bs_plan_destroy(p);
         return st;
     }
     *out = p;
+    return BS_OK;
+}
+
+bs_status bs_plan_device_status(const bs_plan *p, int32_t *flags) {
+    if (!p) return set_error(BS_EINVAL, "NULL plan");
+    int h = 0;
+    cudaError_t e = cudaMemcpy(&h, p->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return bs::cuda_error(e, "device status read");
+    if (flags) *flags = h;
+    if (h) {
+        const int zero = 0;
+        e = cudaMemcpy(p->d_err, &zero, sizeof(int), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return bs::cuda_error(e, "device status reset");
+        return set_error(BS_ETIMEOUT, "a bounded device wait gave up (device error word set)");
+    }
     return BS_OK;
 }
 

@@ -179,8 +179,11 @@ def test_beamspace_full(N, M):
     assert err.max() <= FFT_TOL
 
 
-@pytest.mark.parametrize("F,N", [(16, 1), (64, 7), (512, 33), (4096, 12), (2048, 9)])
+@pytest.mark.parametrize("F,N", [(16, 1), (64, 7), (512, 33), (4096, 12), (2048, 9),
+                                 (2048, 10), (1024, 6), (512, 34), (2048, 1024)])
 def test_channelize_sizes(F, N):
+    """Odd N takes the plain kernel; even N with F in 512..2048 the persistent
+    TMA-staged kernel (ragged last column tile when N % 4 != 0)."""
     rng = np.random.default_rng(F + N)
     Pn, L = 3, min(F, 16)
     x = (rng.standard_normal((Pn, F, N)) + 1j * rng.standard_normal((Pn, F, N))).astype(np.complex64)
@@ -191,9 +194,29 @@ def test_channelize_sizes(F, N):
     P.bs_channelize(plan, xd, xc, P=Pn)
     torch.cuda.synchronize()
     got = xc.cpu().numpy().reshape(Pn, F, N)
+    assert plan.device_status() == 0
     ref = O.channelize(x, L).reshape(Pn, F, N)
     err = np.linalg.norm(got - ref, axis=1) / np.linalg.norm(ref, axis=1)
     assert err.max() <= FFT_TOL
+
+
+def test_channelize_tma_matches_plain_kernel():
+    """The TMA-staged persistent channeliser and the plain one do the same
+    arithmetic in the same order: identical bits."""
+    rng = np.random.default_rng(11)
+    Pn, F, N = 5, 2048, 1022
+    x = (rng.standard_normal((Pn, F, N)) + 1j * rng.standard_normal((Pn, F, N))).astype(np.complex64)
+    xd = torch.from_numpy(x.reshape(-1)).cuda()
+    outs = []
+    for flags in (0, P.BS_FLAG_NO_TMA):
+        plan = P.Plan(N=N, F=F, L=128, M=1024, u=[0.0], W=[1], K=[1], P_train=Pn, P_test=0,
+                      fc=10e9, fs=1e9, fd=10e9, delta=1.0, flags=flags)
+        xc = torch.empty_like(xd)
+        P.bs_channelize(plan, xd, xc, P=Pn)
+        torch.cuda.synchronize()
+        assert plan.device_status() == 0
+        outs.append(xc.cpu())
+    assert torch.equal(outs[0], outs[1])
 
 
 def _solve_only(R_list, a_list, **plan_kw):
