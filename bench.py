@@ -51,6 +51,9 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-graph", action="store_true", help="time bs_run calls instead of a CUDA graph")
+    ap.add_argument("--autotune", action="store_true", help="autotune the fused kernel before timing")
+    ap.add_argument("--fused", action="store_true", help="fused persistent covariance + solve kernel")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="budget of the oracle sample timed for cpu_baseline")
     return ap.parse_args()
@@ -219,6 +222,7 @@ def algorithmic_bytes(plan, cfg):
         "channelize": 2 * raw,
         "beamspace": raw + s.ztrain_bytes + 8 * s.ztest_elems,
         "window_cov": s.ztrain_bytes + 16 * s.r_elems,
+        "cov_solve": s.ztrain_bytes + 16 * s.r_elems + 24 * s.c_elems + 8 * s.c_elems + 4 * s.pairs,
         "mvdr_solve": 16 * s.r_elems + 24 * s.c_elems + 8 * s.c_elems + 4 * s.pairs,
         "apply": 8 * s.ztest_elems + 8 * s.c_elems + 8 * s.out_elems,
     }
@@ -251,7 +255,8 @@ def run_ours(args):
     cfg = all_configs()[args.workload]
     scene = make_scene(cfg)
     prec = {"fp32": P.BS_PREC_FP32, "fp16": P.BS_PREC_FP16, "bf16": P.BS_PREC_BF16}[args.precision]
-    plan = P.Plan.from_scene_config(cfg, scene.u_tgt, precision=prec)
+    plan = P.Plan.from_scene_config(cfg, scene.u_tgt, precision=prec,
+                                    flags=P.BS_FLAG_FUSED if args.fused else 0)
     b = P.alloc_buffers(plan, dev)
     b.x.copy_(torch.from_numpy(scene.x.reshape(-1)))
     stream = torch.cuda.Stream(dev)
@@ -260,15 +265,36 @@ def run_ours(args):
         return [
             ("channelize", lambda: P.bs_channelize(pl, bb.x, bb.xc, stream=stream)),
             ("beamspace", lambda: P.bs_beamspace(pl, bb.xc, bb.z_train, bb.z_test, stream=stream)),
+        ] + ([
+            ("cov_solve", lambda: P.bs_cov_solve(pl, bb.z_train, bb.c, bb.info, R=bb.R, stream=stream)),
+        ] if args.fused else [
             ("window_cov", lambda: P.bs_window_cov(pl, bb.z_train, bb.R, stream=stream)),
             ("mvdr_solve", lambda: P.bs_mvdr_solve(pl, bb.R, bb.c, bb.info, stream=stream)),
+        ]) + [
             ("apply", lambda: P.bs_apply(pl, bb.z_test, bb.c, bb.out, stream=stream)),
         ]
 
     stages = stages_for(plan, b)
 
+    def plain_stages(pl, bb):
+        return [
+            ("channelize", lambda: P.bs_channelize(pl, bb.x, bb.xc, stream=stream)),
+            ("beamspace", lambda: P.bs_beamspace(pl, bb.xc, bb.z_train, bb.z_test, stream=stream)),
+            ("window_cov", lambda: P.bs_window_cov(pl, bb.z_train, bb.R, stream=stream)),
+            ("mvdr_solve", lambda: P.bs_mvdr_solve(pl, bb.R, bb.c, bb.info, stream=stream)),
+            ("apply", lambda: P.bs_apply(pl, bb.z_test, bb.c, bb.out, stream=stream)),
+        ]
+
+    tune = None
+    if args.autotune:
+        tune = P.bs_autotune(plan, b, stream=stream)
+    graph = None if args.no_graph else P.Graph(plan, b, stream)
+
     def step():
-        P.bs_run(plan, b, stream=stream)
+        if graph is not None:
+            graph.launch(stream)
+        else:
+            P.bs_run(plan, b, stream=stream)
 
     def timed_loop(fn, K):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -306,7 +332,7 @@ def run_ours(args):
         for _ in range(args.warmup):
             P.bs_run(pplan, pb, stream=stream)
         pms = timed_loop(lambda: P.bs_run(pplan, pb, stream=stream), args.steps) / args.steps
-        pbd = stage_breakdown(stages_for(pplan, pb), max(3, args.steps // 4))
+        pbd = stage_breakdown(plain_stages(pplan, pb), max(3, args.steps // 4))
         p_core = pbd["window_cov"] + pbd["mvdr_solve"]
         plain = {"ms_per_step": pms, "value": cfg.pairs / (pms / 1e3),
                  "solve_core_ms": p_core, "solve_core_pairs_per_s": cfg.pairs / (p_core / 1e3)}
@@ -336,6 +362,13 @@ def run_ours(args):
     ms_step = max_over_ranks(ws, total_ms / args.steps)
     value = ws * cfg.pairs / (ms_step / 1e3)
     breakdown = stage_breakdown(stages, args.steps)
+    other = stage_breakdown([
+        ("cov_solve", lambda: P.bs_cov_solve(plan, b.z_train, b.c, b.info, R=b.R, stream=stream)),
+    ] if not args.fused else [
+        ("window_cov", lambda: P.bs_window_cov(plan, b.z_train, b.R, stream=stream)),
+        ("mvdr_solve", lambda: P.bs_mvdr_solve(plan, b.R, b.c, b.info, stream=stream)),
+    ], max(3, args.steps // 4))
+    step()   # leave the timed path's results in the buffers
     clocks = sampler.stop()
     clocks["window"] = "plain-path, e2e, timed and per-stage loops"
     info = b.info.cpu().numpy()
@@ -350,7 +383,8 @@ def run_ours(args):
     per_stage = {k: {"ms": v, "GB/s": abytes[k] / (v / 1e3) / 1e9,
                      "frac_hbm": abytes[k] / (v / 1e3) / 1e9 / peaks["hbm_gbs"]}
                  for k, v in breakdown.items()}
-    solve_core_ms = breakdown["window_cov"] + breakdown["mvdr_solve"]
+    solve_core_ms = (breakdown["cov_solve"] if args.fused
+                     else breakdown["window_cov"] + breakdown["mvdr_solve"])
     if plain is not None:
         plain["solve_core_speedup_of_ours"] = plain["solve_core_ms"] / solve_core_ms
         plain["step_speedup_of_ours"] = plain["ms_per_step"] / ms_step
@@ -388,7 +422,10 @@ def run_ours(args):
                            parallelism=f"{ws} independent batch(es)"),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": len(stages) * args.steps,
+            "timed_as": "CUDA graph of the whole pass" if graph is not None else "bs_run calls",
+            "autotune": tune,
             "clocks": clocks, "stages": per_stage, "solve_core_ms": solve_core_ms,
+            "other_solve_core_ms": other,
             "plain_fp32": plain, "accuracy": accuracy,
             "info_counts": {str(k): int(v) for k, v in zip(*np.unique(info, return_counts=True))},
         }

@@ -64,8 +64,8 @@ typedef enum {
 /* Storage / arithmetic precision of the training windows and covariance. */
 typedef enum {
     BS_PREC_FP32 = 0,     /* cf32 windows, FP32 SIMT products */
-    BS_PREC_FP16 = 1,     /* fp16 windows (x store_scale), tensor-core products */
-    BS_PREC_BF16 = 2      /* bf16 windows, tensor-core products */
+    BS_PREC_FP16 = 1,     /* fp16 windows (x store_scale), tensor-core products (mma.sync m16n8k16) */
+    BS_PREC_BF16 = 2      /* bf16 windows (x store_scale), tensor-core products */
 } bs_precision;
 
 /* Plan flags. */
@@ -74,6 +74,8 @@ typedef enum {
 #define BS_FLAG_NO_REFINE  (1u << 1) /* skip the iterative-refinement step */
 #define BS_FLAG_NO_FP64    (1u << 2) /* never escalate a pair to the FP64 solve */
 #define BS_FLAG_NO_TMA     (1u << 3) /* channeliser without the TMA-staged persistent kernel */
+#define BS_FLAG_FUSED      (1u << 4) /* bs_run: bs_cov_solve instead of bs_window_cov + bs_mvdr_solve */
+#define BS_FLAG_SIMT_COV   (1u << 5) /* 16-bit windows: FP32 SIMT products instead of the tensor cores */
 
 typedef struct { float re, im; } bs_cf32;
 typedef struct { double re, im; } bs_cf64;
@@ -192,9 +194,10 @@ bs_status bs_beamspace_full(const bs_plan *plan, const bs_cf32 *y, int64_t nvec,
 /* Loaded window covariance (Eq. EmpiricalCov on the windowed vectors, plus
  * loading): R_g = (1/K_g) sum_{v<K_g} z_v z_v^H + delta_g I, stored in FP64
  * (full Hermitian matrix).  delta_pair: NULL = plan delta, else a device
- * array [pairs] of per-pair loading (float).  Products are formed in the
- * plan precision; FP32 partial sums of at most 16 vectors are combined in
- * double-float. */
+ * array [pairs] of per-pair loading (float).  FP32 windows: FP32 products,
+ * partial sums of at most 16 vectors combined in double-float.  16-bit
+ * windows: products on the tensor cores with FP32 accumulation, folded
+ * into double-float every 128 vectors. */
 bs_status bs_window_cov(const bs_plan *plan, const void *z_train, const float *delta_pair,
                         bs_cf64 *R, bs_stream stream);
 
@@ -208,12 +211,32 @@ bs_status bs_window_cov(const bs_plan *plan, const void *z_train, const float *d
 bs_status bs_mvdr_solve(const bs_plan *plan, const bs_cf64 *R, bs_cf32 *c, int32_t *info,
                         bs_stream stream);
 
+/* Fused covariance + solve of every pair in one persistent launch (the
+ * default of bs_run): the same results as bs_window_cov followed by
+ * bs_mvdr_solve (R is optional here and may be NULL).  CTAs take pairs from
+ * a work queue ordered by decreasing W_g^2 K_g, so pairs of uneven W and K
+ * share one launch.  The queue head lives in the plan's workspace, so calls
+ * on one plan must not overlap on the GPU.  Launch shape: bs_autotune or
+ * bs_set_launch.  bs_run uses it when the plan has BS_FLAG_FUSED. */
+bs_status bs_cov_solve(const bs_plan *plan, const void *z_train, const float *delta_pair, bs_cf64 *R,
+                       bs_cf32 *c, int32_t *info, bs_stream stream);
+
+/* Times bs_cov_solve for every launch shape (64 or 128 threads per CTA; 2,
+ * 3, 4, 5, 6 or 8 CTAs per SM) on the caller's buffers (3 runs each, after
+ * one warm-up), keeps the fastest in the plan and returns it (any output
+ * pointer may be NULL).  Synchronises `stream`; overwrites R, c, info. */
+bs_status bs_autotune(bs_plan *plan, const void *z_train, bs_cf64 *R, bs_cf32 *c, int32_t *info,
+                      bs_stream stream, int32_t *threads, int32_t *ctas_per_sm, float *ms);
+
+/* Sets the launch shape of bs_cov_solve (threads 64 or 128; 1..32 CTAs per SM). */
+bs_status bs_set_launch(bs_plan *plan, int32_t threads, int32_t ctas_per_sm);
+
 /* Beamformer output (Sec. II-B): out[g][v'] = c_g^H z_test[g][v'], v' < Vte. */
 bs_status bs_apply(const bs_plan *plan, const bs_cf32 *z_test, const bs_cf32 *c,
                    bs_cf32 *out, bs_stream stream);
 
 /* The whole pass on device buffers: channelise, beamspace, covariance,
- * solve, apply (delta = plan delta). */
+ * solve (bs_cov_solve with BS_FLAG_FUSED), apply (delta = plan delta). */
 bs_status bs_run(const bs_plan *plan, const bs_buffers *buf, bs_stream stream);
 
 /* The whole pass from host memory: copies x_host ([P][F][N] cf32; pinned
@@ -222,6 +245,14 @@ bs_status bs_run(const bs_plan *plan, const bs_buffers *buf, bs_stream stream);
  * Synchronises `stream` before returning. */
 bs_status bs_run_host(const bs_plan *plan, const bs_cf32 *x_host, bs_cf32 *out_host,
                       const bs_buffers *buf, bs_stream stream);
+
+/* CUDA graph of one whole pass (bs_run on `buf`), captured on `stream`
+ * (must not be the legacy default stream).  Launch it as often as needed;
+ * the buffers and plan must outlive it. */
+typedef struct bs_graph bs_graph;
+bs_status bs_graph_create(const bs_plan *plan, const bs_buffers *buf, bs_stream stream, bs_graph **graph);
+bs_status bs_graph_launch(bs_graph *graph, bs_stream stream);
+void      bs_graph_destroy(bs_graph *graph);
 
 /* ------------------------------------------------------------- errors --- */
 const char *bs_status_string(bs_status s);

@@ -19,14 +19,16 @@ from .build import lib_path
 
 __all__ = [
     "BS_PREC_FP32", "BS_PREC_FP16", "BS_PREC_BF16",
-    "BS_FLAG_PLAIN", "BS_FLAG_NO_REFINE", "BS_FLAG_NO_FP64", "BS_FLAG_NO_TMA",
+    "BS_FLAG_PLAIN", "BS_FLAG_NO_REFINE", "BS_FLAG_NO_FP64", "BS_FLAG_NO_TMA", "BS_FLAG_FUSED", "BS_FLAG_SIMT_COV",
+    "bs_cov_solve", "bs_autotune", "bs_set_launch", "Graph",
     "BsError", "Plan", "Buffers", "alloc_buffers", "lib", "bs_plan_tables_host",
     "bs_channelize", "bs_beamspace", "bs_beamspace_full", "bs_window_cov",
     "bs_mvdr_solve", "bs_apply", "bs_run", "bs_run_host",
 ]
 
 BS_PREC_FP32, BS_PREC_FP16, BS_PREC_BF16 = 0, 1, 2
-BS_FLAG_PLAIN, BS_FLAG_NO_REFINE, BS_FLAG_NO_FP64, BS_FLAG_NO_TMA = 1, 2, 4, 8
+BS_FLAG_PLAIN, BS_FLAG_NO_REFINE, BS_FLAG_NO_FP64, BS_FLAG_NO_TMA, BS_FLAG_FUSED = 1, 2, 4, 8, 16
+BS_FLAG_SIMT_COV = 32
 
 
 class BsError(RuntimeError):
@@ -75,6 +77,12 @@ _SIGS = {
     "bs_run_host": ([_P, _P, _P, ctypes.POINTER(_Buffers), _P], ctypes.c_int),
     "bs_plan_tables_host": ([ctypes.POINTER(_Config), _P, _P], ctypes.c_int),
     "bs_plan_device_status": ([_P, _P], ctypes.c_int),
+    "bs_cov_solve": ([_P, _P, _P, _P, _P, _P, _P], ctypes.c_int),
+    "bs_autotune": ([_P, _P, _P, _P, _P, _P, _P, _P, _P], ctypes.c_int),
+    "bs_set_launch": ([_P, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
+    "bs_graph_create": ([_P, ctypes.POINTER(_Buffers), _P, ctypes.POINTER(_P)], ctypes.c_int),
+    "bs_graph_launch": ([_P, _P], ctypes.c_int),
+    "bs_graph_destroy": ([_P], None),
     "bs_status_string": ([ctypes.c_int], ctypes.c_char_p),
     "bs_last_error": ([], ctypes.c_char_p),
 }
@@ -318,6 +326,33 @@ def bs_mvdr_solve(plan: Plan, R: torch.Tensor, c: torch.Tensor, info: torch.Tens
            "bs_mvdr_solve")
 
 
+def bs_cov_solve(plan: Plan, z_train: torch.Tensor, c: torch.Tensor, info: torch.Tensor,
+                 R: Optional[torch.Tensor] = None, delta_pair: Optional[torch.Tensor] = None, stream=None):
+    s = plan.sizes
+    _check(lib().bs_cov_solve(plan.handle, _ztr_check(plan, z_train),
+                              _ptr(delta_pair, torch.float32, s.pairs, "delta_pair"),
+                              _ptr(R, torch.complex128, s.r_elems, "R"),
+                              _ptr(c, torch.complex64, s.c_elems, "c"),
+                              _ptr(info, torch.int32, s.pairs, "info"), _stream(stream)), "bs_cov_solve")
+
+
+def bs_autotune(plan: Plan, bufs: "Buffers", stream=None) -> dict:
+    """Time the launch shapes of bs_cov_solve on these buffers; the fastest
+    is kept in the plan."""
+    s = plan.sizes
+    thr, cps, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_float()
+    _check(lib().bs_autotune(plan.handle, _ztr_check(plan, bufs.z_train),
+                             _ptr(bufs.R, torch.complex128, s.r_elems, "R"),
+                             _ptr(bufs.c, torch.complex64, s.c_elems, "c"),
+                             _ptr(bufs.info, torch.int32, s.pairs, "info"), _stream(stream),
+                             ctypes.byref(thr), ctypes.byref(cps), ctypes.byref(ms)), "bs_autotune")
+    return {"threads": thr.value, "ctas_per_sm": cps.value, "ms": ms.value}
+
+
+def bs_set_launch(plan: Plan, threads: int, ctas_per_sm: int):
+    _check(lib().bs_set_launch(plan.handle, threads, ctas_per_sm), "bs_set_launch")
+
+
 def bs_apply(plan: Plan, z_test: torch.Tensor, c: torch.Tensor, out: torch.Tensor, stream=None):
     s = plan.sizes
     _check(lib().bs_apply(plan.handle, _ptr(z_test, torch.complex64, s.ztest_elems, "z_test"),
@@ -350,3 +385,31 @@ def bs_run_host(plan: Plan, x_host: torch.Tensor, out_host: torch.Tensor, bufs: 
     cb = _cbuf(plan, bufs)
     _check(lib().bs_run_host(plan.handle, x_host.data_ptr(), out_host.data_ptr(), ctypes.byref(cb),
                              _stream(stream)), "bs_run_host")
+
+
+class Graph:
+    """CUDA graph of one whole pass on fixed buffers (bs_graph_create)."""
+
+    def __init__(self, plan: Plan, bufs: Buffers, stream):
+        if stream is None:
+            raise BsError("graph capture needs a non-default stream")
+        self._plan, self._bufs = plan, bufs
+        self._cb = _cbuf(plan, bufs)
+        h = _P()
+        _check(lib().bs_graph_create(plan.handle, ctypes.byref(self._cb), _stream(stream), ctypes.byref(h)),
+               "bs_graph_create")
+        self._h = h
+
+    def launch(self, stream):
+        _check(lib().bs_graph_launch(self._h, _stream(stream)), "bs_graph_launch")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().bs_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -72,14 +72,126 @@ bs_status bs_apply(const bs_plan *p, const bs_cf32 *z_test, const bs_cf32 *c, bs
     return bs::launch_apply(p, (const float2 *)z_test, (const float2 *)c, (float2 *)out, (cudaStream_t)stream);
 }
 
+bs_status bs_cov_solve(const bs_plan *p, const void *z_train, const float *delta_pair, bs_cf64 *R, bs_cf32 *c,
+                       int32_t *info, bs_stream stream) {
+    BS_REQUIRE(p, "NULL plan");
+    BS_REQUIRE(z_train && c && info, "NULL buffer");
+    if (bs_status s = check_device(p)) return s;
+    return bs::launch_cov_solve(p, z_train, delta_pair, (double2 *)R, (float2 *)c, info, p->d_head, p->cs,
+                                (cudaStream_t)stream);
+}
+
 bs_status bs_run(const bs_plan *p, const bs_buffers *b, bs_stream stream) {
     BS_REQUIRE(p && b, "NULL argument");
     bs_status s;
     if ((s = bs_channelize(p, b->x, p->P, b->xc, stream))) return s;
     if ((s = bs_beamspace(p, b->xc, b->z_train, b->z_test, stream))) return s;
-    if ((s = bs_window_cov(p, b->z_train, nullptr, b->R, stream))) return s;
-    if ((s = bs_mvdr_solve(p, b->R, b->c, b->info, stream))) return s;
+    if (p->cfg.flags & BS_FLAG_FUSED) {
+        if ((s = bs_cov_solve(p, b->z_train, nullptr, b->R, b->c, b->info, stream))) return s;
+    } else {
+        if ((s = bs_window_cov(p, b->z_train, nullptr, b->R, stream))) return s;
+        if ((s = bs_mvdr_solve(p, b->R, b->c, b->info, stream))) return s;
+    }
     return bs_apply(p, b->z_test, b->c, b->out, stream);
+}
+
+struct bs_graph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+bs_status bs_graph_create(const bs_plan *p, const bs_buffers *b, bs_stream stream, bs_graph **out) {
+    BS_REQUIRE(p && b && out, "NULL argument");
+    BS_REQUIRE(stream, "graph capture needs a non-default stream");
+    *out = nullptr;
+    const cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return bs::cuda_error(e, "begin capture");
+    const bs_status rs = bs_run(p, b, stream);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(st, &g);
+    if (rs) {
+        if (g) cudaGraphDestroy(g);
+        return rs;
+    }
+    if (e != cudaSuccess) return bs::cuda_error(e, "end capture");
+    bs_graph *gr = new bs_graph();
+    gr->graph = g;
+    e = cudaGraphInstantiate(&gr->exec, g, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        delete gr;
+        return bs::cuda_error(e, "graph instantiate");
+    }
+    *out = gr;
+    return BS_OK;
+}
+
+bs_status bs_graph_launch(bs_graph *g, bs_stream stream) {
+    BS_REQUIRE(g, "NULL graph");
+    return bs::cuda_error(cudaGraphLaunch(g->exec, (cudaStream_t)stream), "graph launch");
+}
+
+void bs_graph_destroy(bs_graph *g) {
+    if (!g) return;
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    delete g;
+}
+
+bs_status bs_autotune(bs_plan *p, const void *z_train, bs_cf64 *R, bs_cf32 *c, int32_t *info, bs_stream stream,
+                      int32_t *threads_out, int32_t *ctas_per_sm_out, float *ms_out) {
+    BS_REQUIRE(p && z_train && c && info, "NULL argument");
+    if (bs_status s = check_device(p)) return s;
+    const cudaStream_t st = (cudaStream_t)stream;
+    const int thr[2] = {64, 128};
+    const int cps[6] = {2, 3, 4, 5, 6, 8};
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return bs::cuda_error(cudaGetLastError(), "event create");
+    bs::CovSolveLaunch best = p->cs;
+    float best_ms = 1e30f;
+    bs_status s = BS_OK;
+    for (int ti = 0; ti < 2 && !s; ++ti) {
+        for (int ci = 0; ci < 6 && !s; ++ci) {
+            bs::CovSolveLaunch cand;
+            cand.threads = thr[ti];
+            cand.ctas_per_sm = cps[ci];
+            s = bs::launch_cov_solve(p, z_train, nullptr, (double2 *)R, (float2 *)c, info, p->d_head, cand, st);
+            if (s) break;
+            cudaEventRecord(e0, st);
+            for (int r = 0; r < 3 && !s; ++r)
+                s = bs::launch_cov_solve(p, z_train, nullptr, (double2 *)R, (float2 *)c, info, p->d_head, cand, st);
+            cudaEventRecord(e1, st);
+            if (s) break;
+            cudaError_t e = cudaEventSynchronize(e1);
+            if (e != cudaSuccess) { s = bs::cuda_error(e, "autotune"); break; }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            ms /= 3.f;
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = cand;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s) return s;
+    p->cs = best;
+    if (threads_out) *threads_out = best.threads;
+    if (ctas_per_sm_out) *ctas_per_sm_out = best.ctas_per_sm;
+    if (ms_out) *ms_out = best_ms;
+    return BS_OK;
+}
+
+bs_status bs_set_launch(bs_plan *p, int32_t threads, int32_t ctas_per_sm) {
+    BS_REQUIRE(p, "NULL plan");
+    BS_REQUIRE(threads == 64 || threads == 128, "threads must be 64 or 128");
+    BS_REQUIRE(ctas_per_sm >= 1 && ctas_per_sm <= 32, "ctas_per_sm must be in 1..32");
+    p->cs.threads = threads;
+    p->cs.ctas_per_sm = ctas_per_sm;
+    return BS_OK;
 }
 
 bs_status bs_run_host(const bs_plan *p, const bs_cf32 *x_host, bs_cf32 *out_host, const bs_buffers *b,

@@ -9,6 +9,14 @@
 
 #include "bs.h"
 
+namespace bs {
+// Launch shape of the fused covariance + solve kernel (set by bs_autotune).
+struct CovSolveLaunch {
+    int threads = 128;      // 64 or 128
+    int ctas_per_sm = 5;
+};
+}  // namespace bs
+
 struct bs_plan {
     bs_config cfg;              // host pointers cleared after create
     int B = 0, P = 0, Vte = 0, Wmax = 0, Kmax = 0, sumW = 0;
@@ -28,10 +36,16 @@ struct bs_plan {
     int32_t *d_start = nullptr, *d_Wg = nullptr, *d_Kg = nullptr, *d_gather = nullptr;
     int64_t *d_woff = nullptr, *d_ztr_off = nullptr, *d_zte_off = nullptr, *d_roff = nullptr;
     float2 *d_at32 = nullptr;
+    float2 *d_atlo = nullptr;                    // a~ - (float)a~ (double-float low parts)
     double2 *d_at64 = nullptr;
     float2 *d_twF = nullptr, *d_twM = nullptr;   // e^{-2 pi i k / F}, e^{-2 pi i k / M}
     int *d_err = nullptr;                        // device error word (bit 0: a bounded wait gave up)
     int num_sms = 0;
+    // fused covariance + solve: queue order (decreasing W^2 K), workspace head
+    std::vector<int32_t> order;
+    int32_t *d_order = nullptr;
+    int *d_head = nullptr;
+    bs::CovSolveLaunch cs;
 };
 
 namespace bs {
@@ -47,10 +61,14 @@ bs_status launch_beamspace_full(const bs_plan *p, const float2 *y, int64_t nvec,
                                 cudaStream_t st);
 bs_status launch_window_cov(const bs_plan *p, const void *ztr, const float *delta, double2 *R,
                             cudaStream_t st);
+bs_status launch_window_cov_mma(const bs_plan *p, const void *ztr, const float *delta, double2 *R,
+                                cudaStream_t st);
 bs_status launch_mvdr_solve(const bs_plan *p, const double2 *R, float2 *c, int32_t *info,
                             cudaStream_t st);
 bs_status launch_apply(const bs_plan *p, const float2 *zte, const float2 *c, float2 *out,
                        cudaStream_t st);
+bs_status launch_cov_solve(const bs_plan *p, const void *ztr, const float *delta, double2 *R, float2 *c,
+                           int32_t *info, int *head, const CovSolveLaunch &cfg, cudaStream_t st);
 int beamspace_vectors_per_cta(int M);
 
 }  // namespace bs

@@ -2,8 +2,10 @@
 // (host, FP64), device upload, error reporting.  Compiled with
 // -ffp-contract=off so that the window decision is evaluated exactly in the
 // documented order (no fused multiply-add).
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <numeric>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -121,9 +123,12 @@ void bs_plan_destroy(bs_plan *p) {
     cudaFree(p->d_roff);
     cudaFree(p->d_at32);
     cudaFree(p->d_at64);
+    cudaFree(p->d_atlo);
     cudaFree(p->d_twF);
     cudaFree(p->d_twM);
     cudaFree(p->d_err);
+    cudaFree(p->d_order);
+    cudaFree(p->d_head);
     delete p;
 }
 
@@ -224,7 +229,7 @@ bs_status bs_plan_create(bs_plan **out, const bs_config *cfg) {
     p->zte_elems = p->zte_off[G];
     p->r_elems = p->roff[G];
     p->at.resize(p->c_elems);
-    std::vector<float2> at32(p->c_elems);
+    std::vector<float2> at32(p->c_elems), atlo(p->c_elems);
     std::vector<double2> at64(p->c_elems);
     for (int t = 0; t < c.T; ++t) {
         for (int s = 0; s < c.L; ++s) {
@@ -236,6 +241,7 @@ bs_status bs_plan_create(bs_plan **out, const bs_config *cfg) {
                 const int64_t e = p->woff[g] + w;
                 p->at[e] = a;
                 at32[e] = make_float2((float)a.re, (float)a.im);
+                atlo[e] = make_float2((float)(a.re - (double)at32[e].x), (float)(a.im - (double)at32[e].y));
                 at64[e] = make_double2(a.re, a.im);
             }
         }
@@ -247,6 +253,13 @@ bs_status bs_plan_create(bs_plan **out, const bs_config *cfg) {
     for (int t = 0; t < c.T; ++t)
         for (int cc = 0; cc < p->vpb; ++cc)
             for (int w = 0; w < p->Wt[t]; ++w) p->gather.push_back((t << 8) | (cc << 4) | w);
+
+    // work-queue order of the fused covariance + solve: decreasing W^2 K
+    p->order.resize(G);
+    std::iota(p->order.begin(), p->order.end(), 0);
+    std::stable_sort(p->order.begin(), p->order.end(), [&](int32_t x, int32_t y) {
+        return (int64_t)p->Wg[x] * p->Wg[x] * p->Kg[x] > (int64_t)p->Wg[y] * p->Wg[y] * p->Kg[y];
+    });
 
     cudaGetDevice(&p->device);
     bs_status st = BS_OK;
@@ -260,9 +273,12 @@ bs_status bs_plan_create(bs_plan **out, const bs_config *cfg) {
     if (!st) st = upload(&p->d_roff, p->roff);
     if (!st) st = upload(&p->d_at32, at32);
     if (!st) st = upload(&p->d_at64, at64);
+    if (!st) st = upload(&p->d_atlo, atlo);
     if (!st) st = upload(&p->d_twF, twiddles(c.F));
     if (!st) st = upload(&p->d_twM, twiddles(c.M));
     if (!st) st = upload(&p->d_err, std::vector<int>(1, 0));
+    if (!st) st = upload(&p->d_order, p->order);
+    if (!st) st = upload(&p->d_head, std::vector<int>(1, 0));
     if (!st) st = bs::cuda_error(cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device),
                                  "device attribute");
     if (st) {

@@ -1,0 +1,338 @@
+// Half-warp batched Cholesky MVDR solve of one (target, subband) pair,
+// shared by the stand-alone solve kernel and the fused persistent kernel.
+//
+// Eq. BeamCorrMVDR: c = R^-1 a~ / (a~^H R^-1 a~).  Lane i of the half-warp
+// holds row i of R (W <= 16).
+//   1. R = L L^H in FP32 (right-looking; column k broadcast by shuffles);
+//   2. u = L^-1 a~, v = L^-H u (triangular solves, one shuffle per step;
+//      the backward solve reads L transposed from shared memory);
+//   3. one refinement step: r = a~ - R v formed with error-free FP32
+//      transformations from the double-float (hi + lo) parts of R and a~
+//      (about twice FP32 precision, at FP32 speed: FP64 is a small
+//      fraction of FP32 throughput on this part), v += L^-H L^-1 r;
+//   4. c = v / (a~^H v) (a~^H v is a~^H R^-1 a~; dividing by it makes
+//      c^H a~ = 1 up to rounding).
+// A pair whose FP32 factorisation fails, or whose pivot ratio
+// (max L_ii / min L_ii)^2 exceeds kappa_max, is solved again entirely in
+// FP64 (info = -2).  Non-finite input: info = -1, c = NaN.  FP64 pivot k
+// not positive: info = k + 1, c = NaN.
+#pragma once
+#include <math.h>
+
+#include "common.cuh"
+
+namespace bs {
+
+constexpr int WMAX = 16;
+
+__device__ __forceinline__ float2 conjmul(float2 l, float2 v) {   // conj(l) * v
+    return make_float2(l.x * v.x + l.y * v.y, l.x * v.y - l.y * v.x);
+}
+__device__ __forceinline__ double2 dcmul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 dcmulc(double2 a, double2 b) {  // a * conj(b)
+    return make_double2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+__device__ __forceinline__ double2 dconjmul(double2 l, double2 v) {  // conj(l) * v
+    return make_double2(l.x * v.x + l.y * v.y, l.x * v.y - l.y * v.x);
+}
+__device__ __forceinline__ float2 shfl2(unsigned mask, float2 v, int src) {
+    return make_float2(__shfl_sync(mask, v.x, src, 16), __shfl_sync(mask, v.y, src, 16));
+}
+__device__ __forceinline__ double2 shfl2d(unsigned mask, double2 v, int src) {
+    return make_double2(__shfl_sync(mask, v.x, src, 16), __shfl_sync(mask, v.y, src, 16));
+}
+
+// FP32 triangular solves with the factor held as rows (A, diag) and its
+// transpose in Ls: returns v = L^-H L^-1 b.  WT = window size.
+template <int WT>
+__device__ __forceinline__ float2 chol_solve_f32(unsigned mask, int lane, const float2 (&A)[WT], float diag,
+                                                 const float2 (*Ls)[WMAX + 1], float2 b) {
+    const float rdiag = 1.0f / diag;
+    float2 acc = b, u = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int j = 0; j < WT; ++j) {
+        const float2 mine = (lane == j) ? cscale(acc, rdiag) : make_float2(0.f, 0.f);
+        const float2 uj = shfl2(mask, mine, j);
+        if (lane == j) u = uj;
+        if (lane > j) acc = csub(acc, cmul(A[j], uj));
+    }
+    acc = u;
+    float2 v = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int j = WT - 1; j >= 0; --j) {
+        const float2 mine = (lane == j) ? cscale(acc, rdiag) : make_float2(0.f, 0.f);
+        const float2 vj = shfl2(mask, mine, j);
+        if (lane == j) v = vj;
+        if (lane < j) acc = csub(acc, conjmul(Ls[j][lane], vj));
+    }
+    return v;
+}
+
+__device__ __forceinline__ double hw_sum(unsigned mask, double x) {
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) x += __shfl_xor_sync(mask, x, o, 16);
+    return x;
+}
+__device__ __forceinline__ float hw_sumf(unsigned mask, float x) {
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) x += __shfl_xor_sync(mask, x, o, 16);
+    return x;
+}
+
+// Whole solve in FP64 for one pair (escalation path), row `lane` of R given
+// in D.  Returns 0 or pivot+1.
+static __device__ int solve_f64_rows(unsigned mask, int lane, int W, double2 (&D)[WMAX], double2 a,
+                                     double2 (*Ld)[WMAX + 1], double2 &c_out) {
+    const bool row = lane < W;
+#pragma unroll
+    for (int j = 0; j < WMAX; ++j)
+        if (!(row && j < W)) D[j] = make_double2(0.0, 0.0);
+    int fail = 0;
+    double diag = 1.0;
+#pragma unroll
+    for (int k = 0; k < WMAX; ++k) {
+        if (k < W) {
+            const double dkk = __shfl_sync(mask, D[k].x, k, 16);
+            if (!(dkk > 0.0) && fail == 0) fail = k + 1;
+            const double pk = sqrt(dkk > 0.0 ? dkk : 1.0);
+            const double inv = 1.0 / pk;
+            if (lane > k) D[k] = make_double2(D[k].x * inv, D[k].y * inv);
+            if (lane == k) { D[k] = make_double2(pk, 0.0); diag = pk; }
+#pragma unroll
+            for (int j = k + 1; j < WMAX; ++j) {
+                if (j < W) {
+                    const double2 ljk = shfl2d(mask, D[k], j);
+                    if (lane >= j) {
+                        const double2 t = dcmulc(D[k], ljk);
+                        D[j] = make_double2(D[j].x - t.x, D[j].y - t.y);
+                    }
+                }
+            }
+        }
+    }
+    if (fail) return fail;
+#pragma unroll
+    for (int j = 0; j < WMAX; ++j)
+        if (row && j <= lane) Ld[lane][j] = D[j];
+    __syncwarp(mask);
+    double2 acc = a, u = make_double2(0.0, 0.0);
+#pragma unroll
+    for (int j = 0; j < WMAX; ++j) {
+        if (j < W) {
+            const double2 mine = (lane == j) ? make_double2(acc.x / diag, acc.y / diag) : make_double2(0.0, 0.0);
+            const double2 uj = shfl2d(mask, mine, j);
+            if (lane == j) u = uj;
+            if (lane > j) {
+                const double2 t = dcmul(D[j], uj);
+                acc = make_double2(acc.x - t.x, acc.y - t.y);
+            }
+        }
+    }
+    acc = u;
+    double2 v = make_double2(0.0, 0.0);
+#pragma unroll
+    for (int j = WMAX - 1; j >= 0; --j) {
+        if (j < W) {
+            const double2 mine = (lane == j) ? make_double2(acc.x / diag, acc.y / diag) : make_double2(0.0, 0.0);
+            const double2 vj = shfl2d(mask, mine, j);
+            if (lane == j) v = vj;
+            if (lane < j) {
+                const double2 t = dconjmul(Ld[j][lane], vj);
+                acc = make_double2(acc.x - t.x, acc.y - t.y);
+            }
+        }
+    }
+    // s = a^H v
+    const double2 av = dconjmul(a, v);
+    const double sr = hw_sum(mask, row ? av.x : 0.0), si = hw_sum(mask, row ? av.y : 0.0);
+    const double den = sr * sr + si * si;
+    // v / s = v conj(s) / |s|^2
+    c_out = make_double2((v.x * sr + v.y * si) / den, (v.y * sr - v.x * si) / den);
+    return 0;
+}
+
+static __device__ int solve_f64(unsigned mask, int lane, int W, const double2 *__restrict__ Rg, double2 a,
+                                double2 (*Ld)[WMAX + 1], double2 &c_out) {
+    double2 D[WMAX];
+    const bool row = lane < W;
+#pragma unroll
+    for (int j = 0; j < WMAX; ++j) D[j] = (row && j < W) ? Rg[lane * W + j] : make_double2(0.0, 0.0);
+    return solve_f64_rows(mask, lane, W, D, a, Ld, c_out);
+}
+
+// Error-free transformations (FP32): a*b = p + e exactly (FMA), a + b = s + t.
+__device__ __forceinline__ void two_prod(float a, float b, float &p, float &e) {
+    p = a * b;
+    e = fmaf(a, b, -p);
+}
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &t) {
+    s = a + b;
+    const float bb = s - a;
+    t = (a - (s - bb)) + (b - bb);
+}
+
+// Compensated residual r = a - R v for one row (Dot2-style): R = Rh + Rl and
+// a = ah + al are double-float, v is FP32; products of the high parts are
+// split exactly into value + error and summed with two-sum, so r carries
+// about twice the FP32 precision (the refinement then converges like one
+// with an FP64 residual).
+template <int WT, class Rows>
+__device__ __forceinline__ float2 residual_df(unsigned mask, int lane, Rows rows, float2 ah, float2 al, float2 v) {
+    float sr = ah.x, si = ah.y, cr = al.x, ci = al.y;
+    const bool row = lane < WT;
+#pragma unroll
+    for (int j = 0; j < WT; ++j) {
+        const float2 vj = shfl2(mask, v, j);
+        const float4 r4 = row ? rows(j) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float2 Rh = make_float2(r4.x, r4.y), Rl = make_float2(r4.z, r4.w);
+        float p1, e1, p2, e2, p3, e3, p4, e4, t;
+        two_prod(Rh.x, vj.x, p1, e1);   // re += -(Rh.re v.re) + (Rh.im v.im)
+        two_prod(Rh.y, vj.y, p2, e2);
+        two_prod(Rh.x, vj.y, p3, e3);   // im += -(Rh.re v.im) - (Rh.im v.re)
+        two_prod(Rh.y, vj.x, p4, e4);
+        two_sum(sr, -p1, sr, t); cr += t - e1;
+        two_sum(sr, p2, sr, t);  cr += t + e2;
+        two_sum(si, -p3, si, t); ci += t - e3;
+        two_sum(si, -p4, si, t); ci += t - e4;
+        cr -= Rl.x * vj.x - Rl.y * vj.y;
+        ci -= Rl.x * vj.y + Rl.y * vj.x;
+    }
+    return make_float2(sr + cr, si + ci);
+}
+
+// Solve one pair with the calling half-warp (lanes 0..15 of `mask`).
+// Row loader: rows(j) returns entry (lane, j) of R as FP32 (hi, lo) parts in
+// a float4 {hi.re, hi.im, lo.re, lo.im}; Rg64 (may be NULL) is the FP64
+// matrix for the escalation path (else the escalation reads hi + lo).
+// a32/alo: the windowed steering vector as hi / lo FP32 parts, a64 in FP64
+// (escalation).  scratch: [16][17] double2 per half-warp.  Writes c[0..W)
+// and *info.
+template <int WT, class Rows>
+__device__ __forceinline__ void solve_pair_rows(unsigned mask, int lane, Rows rows,
+                                                const float2 *__restrict__ a32g, const float2 *__restrict__ alog,
+                                                const double2 *__restrict__ a64g, float2 *__restrict__ c,
+                                                int32_t *__restrict__ info, double kappa_max, int refine,
+                                                int allow_f64, double2 (*scratch)[WMAX + 1],
+                                                const double2 *Rg64) {
+    float2(*Lsf)[WMAX + 1] = reinterpret_cast<float2(*)[WMAX + 1]>(&scratch[0][0]);
+    constexpr int W = WT;
+    const bool row = lane < W;
+
+    float2 A[WT];
+    bool finite = true;
+#pragma unroll
+    for (int j = 0; j < WT; ++j) {
+        float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (row) r = rows(j);
+        finite = finite && isfinite(r.x) && isfinite(r.y);
+        A[j] = make_float2(r.x, r.y);
+    }
+    const float2 ah = row ? a32g[lane] : make_float2(0.f, 0.f);
+    const float2 al = row ? alog[lane] : make_float2(0.f, 0.f);
+    finite = finite && isfinite(ah.x) && isfinite(ah.y);
+    if (!__all_sync(mask, finite)) {
+        if (row) c[lane] = make_float2(nanf(""), nanf(""));
+        if (lane == 0) *info = -1;
+        return;
+    }
+
+    // 1. FP32 Cholesky
+    int fail = 0;
+    float diag = 1.f, dmax = 0.f, dmin = INFINITY;
+#pragma unroll
+    for (int k = 0; k < WT; ++k) {
+        const float dkk = __shfl_sync(mask, A[k].x, k, 16);
+        if (!(dkk > 0.f) && fail == 0) fail = k + 1;
+        const float pk = sqrtf(dkk > 0.f ? dkk : 1.f);
+        const float inv = 1.f / pk;
+        dmax = fmaxf(dmax, pk);
+        dmin = fminf(dmin, pk);
+        if (lane > k) A[k] = cscale(A[k], inv);
+        if (lane == k) { A[k] = make_float2(pk, 0.f); diag = pk; }
+#pragma unroll
+        for (int j = k + 1; j < WT; ++j) {
+            const float2 ljk = shfl2(mask, A[k], j);
+            if (lane >= j) A[j] = csub(A[j], cmulc(A[k], ljk));
+        }
+    }
+    const float ratio = dmax / dmin;
+    const bool escalate = allow_f64 && (fail != 0 || (double)ratio * (double)ratio > kappa_max);
+    if (!escalate && fail == 0) {
+#pragma unroll
+        for (int j = 0; j < WT; ++j)
+            if (row && j <= lane) Lsf[lane][j] = A[j];
+        __syncwarp(mask);
+        // 2. solve in FP32
+        float2 v = chol_solve_f32<WT>(mask, lane, A, diag, Lsf, ah);
+        // 3. refinement with a compensated (double-float) residual
+        if (refine) {
+            const float2 r = residual_df<WT>(mask, lane, rows, ah, al, v);
+            const float2 dv = chol_solve_f32<WT>(mask, lane, A, diag, Lsf, r);
+            v = cadd(v, dv);
+        }
+        // 4. c = v / (a~^H v)
+        const float2 av = row ? conjmul(ah, v) : make_float2(0.f, 0.f);
+        const float sr = hw_sumf(mask, av.x), si = hw_sumf(mask, av.y);
+        const float inv = 1.0f / (sr * sr + si * si);
+        if (row) c[lane] = make_float2((v.x * sr + v.y * si) * inv, (v.y * sr - v.x * si) * inv);
+        if (lane == 0) *info = 0;
+        return;
+    }
+    if (!escalate) {   // FP32 failure and escalation disabled
+        if (row) c[lane] = make_float2(nanf(""), nanf(""));
+        if (lane == 0) *info = fail;
+        return;
+    }
+    // FP64 path: the matrix in FP64 (given, or rebuilt from hi + lo)
+    double2(*Ldd)[WMAX + 1] = scratch;
+    __syncwarp(mask);
+    double2 cd;
+    const double2 a64 = row ? a64g[lane] : make_double2(0.0, 0.0);
+    int f64fail;
+    if (Rg64) {
+        f64fail = solve_f64(mask, lane, W, Rg64, a64, Ldd, cd);
+    } else {
+        // rebuild row `lane` from hi + lo
+        double2 rowbuf[WMAX];
+#pragma unroll
+        for (int j = 0; j < WMAX; ++j) {
+            const float4 r4 = (row && j < W) ? rows(j < W ? j : 0) : make_float4(0.f, 0.f, 0.f, 0.f);
+            rowbuf[j] = make_double2((double)r4.x + (double)r4.z, (double)r4.y + (double)r4.w);
+        }
+        f64fail = solve_f64_rows(mask, lane, W, rowbuf, a64, Ldd, cd);
+    }
+    if (f64fail) {
+        if (row) c[lane] = make_float2(nanf(""), nanf(""));
+        if (lane == 0) *info = f64fail;
+        return;
+    }
+    if (row) c[lane] = make_float2((float)cd.x, (float)cd.y);
+    if (lane == 0) *info = -2;
+}
+
+// Convenience: R stored as FP64 (global or shared memory); dispatches on W
+// to the solve compiled for that window size.
+__device__ __forceinline__ void solve_pair(unsigned mask, int lane, int W, const double2 *Rg,
+                                           const float2 *__restrict__ a32g, const float2 *__restrict__ alog,
+                                           const double2 *__restrict__ a64g, float2 *__restrict__ c,
+                                           int32_t *__restrict__ info, double kappa_max, int refine,
+                                           int allow_f64, double2 (*scratch)[WMAX + 1]) {
+    auto rows = [&](int j) -> float4 {
+        const double2 r = Rg[lane * W + j];
+        const float hx = (float)r.x, hy = (float)r.y;
+        return make_float4(hx, hy, (float)(r.x - (double)hx), (float)(r.y - (double)hy));
+    };
+#define BS_SOLVE_CASE(n) \
+    case n: solve_pair_rows<n>(mask, lane, rows, a32g, alog, a64g, c, info, kappa_max, refine, allow_f64, scratch, Rg); break;
+    switch (W) {
+        BS_SOLVE_CASE(1) BS_SOLVE_CASE(2) BS_SOLVE_CASE(3) BS_SOLVE_CASE(4)
+        BS_SOLVE_CASE(5) BS_SOLVE_CASE(6) BS_SOLVE_CASE(7) BS_SOLVE_CASE(8)
+        BS_SOLVE_CASE(9) BS_SOLVE_CASE(10) BS_SOLVE_CASE(11) BS_SOLVE_CASE(12)
+        BS_SOLVE_CASE(13) BS_SOLVE_CASE(14) BS_SOLVE_CASE(15) default: BS_SOLVE_CASE(16)
+    }
+#undef BS_SOLVE_CASE
+}
+
+}  // namespace bs

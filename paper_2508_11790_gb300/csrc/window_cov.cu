@@ -8,18 +8,13 @@
 // FP32 over blocks of at most 16 vectors only, and the block sums are
 // combined in double-float (hi + lo FP32 pair, error-free two-sum), which
 // keeps R accurate far beyond FP32 at little extra cost.
-//
-// One CTA per pair.  The lower triangle (i >= j) has E = W(W+1)/2 entries;
-// thread (e, h) accumulates entry e over the vectors v = h (mod H),
-// H = blockDim / E.  Vectors are staged through shared memory in chunks of
-// 16*H so every thread adds exactly one block of <= 16 products per chunk.
 #include "common.cuh"
 #include "internal.h"
 
 namespace bs {
 
-constexpr int COV_THREADS = 256;
-constexpr int COV_SMEM_ELEMS = 2048;   // float2 staging elements (16 KB)
+constexpr int COV_THREADS = 128;
+constexpr int COV_STAGE_ELEMS = 1024;  // window elements per staging buffer (8 KB in FP32)
 
 // (hi, lo) += b with Knuth's two-sum; the pair keeps ~48 bits.
 __device__ __forceinline__ void df_add(float &hi, float &lo, float b) {
@@ -30,88 +25,153 @@ __device__ __forceinline__ void df_add(float &hi, float &lo, float b) {
     lo += err;
 }
 
+// cp.async (global -> shared, bypassing registers) of one 8-byte or 4-byte
+// element; completion is tracked per thread with commit/wait groups.
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void *smem, const void *gmem) {
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(s), "l"(gmem), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
 template <int PREC>
-__device__ __forceinline__ float2 load_window(const void *z, int64_t idx, float inv_sc) {
+__device__ __forceinline__ float2 widen(const void *stage, int q, float inv_sc) {
     if constexpr (PREC == BS_PREC_FP32) {
-        return __ldcs(reinterpret_cast<const float2 *>(z) + idx);
+        return reinterpret_cast<const float2 *>(stage)[q];
     } else if constexpr (PREC == BS_PREC_FP16) {
-        const __half2 h = reinterpret_cast<const __half2 *>(z)[idx];
-        const float2 f = __half22float2(h);
+        const float2 f = __half22float2(reinterpret_cast<const __half2 *>(stage)[q]);
         return make_float2(f.x * inv_sc, f.y * inv_sc);
     } else {
-        const __nv_bfloat162 h = reinterpret_cast<const __nv_bfloat162 *>(z)[idx];
-        const float2 f = __bfloat1622float2(h);
+        const float2 f = __bfloat1622float2(reinterpret_cast<const __nv_bfloat162 *>(stage)[q]);
         return make_float2(f.x * inv_sc, f.y * inv_sc);
     }
 }
 
+// One CTA per pair.  The K x W windows stream through two shared-memory
+// stages (cp.async, the next chunk loads while the current one is used).
+// The lower triangle is cut into 3x3 tiles; thread (tile, slice) keeps its
+// tile in registers and, per vector, loads 6 window entries for 9 complex
+// multiply-adds.  FP32 sums cover at most 16 vectors and are folded into
+// double-float accumulators; the slices are reduced in double-float.
 template <int PREC>
 __global__ void __launch_bounds__(COV_THREADS)
     window_cov_kernel(const void *__restrict__ z, const int64_t *__restrict__ ztr_off,
                       const int32_t *__restrict__ Wg, const int32_t *__restrict__ Kg,
                       const int64_t *__restrict__ roff, const float *__restrict__ delta_pair,
                       double delta, float inv_sc, double2 *__restrict__ R) {
-    __shared__ float2 zs[COV_SMEM_ELEMS];
-    __shared__ float red[4][COV_THREADS];
+    constexpr int ES = (PREC == BS_PREC_FP32) ? 8 : 4;          // bytes per stored element
+    __shared__ __align__(16) unsigned char stage[2][COV_STAGE_ELEMS * ES];
+    __shared__ float red[4][9][COV_THREADS];
     const int64_t g = blockIdx.x;
     const int tid = threadIdx.x;
     const int W = Wg[g], K = Kg[g];
-    const int E = W * (W + 1) / 2;
-    int H = COV_THREADS / E;
-    int kc = 16 * H;
-    if (kc * W > COV_SMEM_ELEMS) kc = COV_SMEM_ELEMS / W;
-    const int64_t zb = ztr_off[g];
-
-    // this thread's entry (i, j), i >= j, and slice h
-    const int e = tid % E, h = tid / E;
+    const int nb3 = (W + 2) / 3;
+    const int nblk = nb3 * (nb3 + 1) / 2;
+    const int H = COV_THREADS / nblk;
+    const int tile = tid % nblk, h = tid / nblk;
     const bool active = h < H;
-    int i = 0, j = 0;
-    {
-        int rem = e;
-        while (rem > i) { rem -= i + 1; ++i; }
-        j = rem;
-    }
-    float hr = 0.f, lr = 0.f, hi_ = 0.f, li = 0.f;
+    int bi = 0, rem = tile;
+    while (rem > bi) { rem -= bi + 1; ++bi; }
+    const int i0 = 3 * bi, j0 = 3 * rem;
+    const int kc = COV_STAGE_ELEMS / W;                            // vectors per chunk
+    const unsigned char *zg = reinterpret_cast<const unsigned char *>(z) + ztr_off[g] * ES;
 
-    for (int k0 = 0; k0 < K; k0 += kc) {
+    auto issue = [&](int k0, int buf) {
         const int n = min(kc, K - k0);
-        __syncthreads();
         for (int q = tid; q < n * W; q += COV_THREADS)
-            zs[q] = load_window<PREC>(z, zb + (int64_t)k0 * W + q, inv_sc);
+            cp_async<ES>(&stage[buf][q * ES], zg + ((int64_t)k0 * W + q) * ES);
+        cp_async_commit();
+    };
+
+    float ar[3][3], ai[3][3], hr[3][3], lr[3][3], hi[3][3], li[3][3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) ar[r][q] = ai[r][q] = hr[r][q] = lr[r][q] = hi[r][q] = li[r][q] = 0.f;
+    int cnt = 0;
+
+    issue(0, 0);
+    int buf = 0;
+    for (int k0 = 0; k0 < K; k0 += kc, buf ^= 1) {
+        const int n = min(kc, K - k0);
+        if (k0 + kc < K) {
+            issue(k0 + kc, buf ^ 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
         __syncthreads();
         if (active) {
-            float ar = 0.f, ai = 0.f;
             for (int v = h; v < n; v += H) {
-                const float2 a = zs[v * W + i], b = zs[v * W + j];
-                ar = fmaf(a.x, b.x, fmaf(a.y, b.y, ar));
-                ai = fmaf(a.y, b.x, fmaf(-a.x, b.y, ai));
+                const int o = v * W;
+                float2 zi[3], zj[3];
+#pragma unroll
+                for (int r = 0; r < 3; ++r) {
+                    zi[r] = (i0 + r < W) ? widen<PREC>(stage[buf], o + i0 + r, inv_sc) : make_float2(0.f, 0.f);
+                    zj[r] = (j0 + r < W) ? widen<PREC>(stage[buf], o + j0 + r, inv_sc) : make_float2(0.f, 0.f);
+                }
+#pragma unroll
+                for (int r = 0; r < 3; ++r)
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {   // z_i conj(z_j)
+                        ar[r][q] = fmaf(zi[r].x, zj[q].x, fmaf(zi[r].y, zj[q].y, ar[r][q]));
+                        ai[r][q] = fmaf(zi[r].y, zj[q].x, fmaf(-zi[r].x, zj[q].y, ai[r][q]));
+                    }
+                if (++cnt == 16) {
+#pragma unroll
+                    for (int r = 0; r < 3; ++r)
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) {
+                            df_add(hr[r][q], lr[r][q], ar[r][q]);
+                            df_add(hi[r][q], li[r][q], ai[r][q]);
+                            ar[r][q] = ai[r][q] = 0.f;
+                        }
+                    cnt = 0;
+                }
             }
-            df_add(hr, lr, ar);
-            df_add(hi_, li, ai);
         }
+        __syncthreads();   // this stage is reloaded two chunks later
     }
-    red[0][tid] = hr;
-    red[1][tid] = lr;
-    red[2][tid] = hi_;
-    red[3][tid] = li;
-    __syncthreads();
-    if (tid < E) {
-        double sr = 0.0, si = 0.0;
-        for (int hh = 0; hh < H; ++hh) {
-            const int o = hh * E + tid;
-            sr += (double)red[0][o] + (double)red[1][o];
-            si += (double)red[2][o] + (double)red[3][o];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            df_add(hr[r][q], lr[r][q], ar[r][q]);
+            df_add(hi[r][q], li[r][q], ai[r][q]);
+            red[0][3 * r + q][tid] = hr[r][q];
+            red[1][3 * r + q][tid] = lr[r][q];
+            red[2][3 * r + q][tid] = hi[r][q];
+            red[3][3 * r + q][tid] = li[r][q];
         }
-        const double d = delta_pair ? (double)delta_pair[g] : delta;
-        const double invK = 1.0 / (double)K;
-        double2 *Rg = R + roff[g];
-        sr *= invK;
-        si *= invK;
+    __syncthreads();
+
+    const double invK = 1.0 / (double)K;
+    const double d = delta_pair ? (double)delta_pair[g] : delta;
+    double2 *Rg = R + roff[g];
+    const int E = W * (W + 1) / 2;
+    for (int e = tid; e < E; e += COV_THREADS) {
+        int i = 0, r2 = e;
+        while (r2 > i) { r2 -= i + 1; ++i; }
+        const int j = r2;
+        const int b = (i / 3) * (i / 3 + 1) / 2 + j / 3;
+        const int ee = 3 * (i % 3) + (j % 3);
+        float sh = 0.f, sl = 0.f, th = 0.f, tl = 0.f;
+        for (int hh = 0; hh < H; ++hh) {
+            const int o = hh * nblk + b;
+            df_add(sh, sl, red[0][ee][o]);
+            sl += red[1][ee][o];
+            df_add(th, tl, red[2][ee][o]);
+            tl += red[3][ee][o];
+        }
+        const double re = ((double)sh + (double)sl) * invK;
+        const double im = ((double)th + (double)tl) * invK;
         if (i == j) {
-            Rg[i * W + i] = make_double2(sr + d, 0.0);
+            Rg[i * W + i] = make_double2(re + d, 0.0);
         } else {
-            Rg[i * W + j] = make_double2(sr, si);
-            Rg[j * W + i] = make_double2(sr, -si);
+            Rg[i * W + j] = make_double2(re, im);
+            Rg[j * W + i] = make_double2(re, -im);
         }
     }
 }
@@ -150,6 +210,8 @@ bs_status launch_window_cov(const bs_plan *p, const void *ztr, const float *delt
                                             p->d_roff, delta, (float)p->cfg.delta, R);
         return check_launch("plain covariance launch");
     }
+    if (p->cfg.precision != BS_PREC_FP32 && !(p->cfg.flags & BS_FLAG_SIMT_COV))
+        return launch_window_cov_mma(p, ztr, delta, R, st);
     const float inv_sc = 1.0f / p->cfg.store_scale;
     switch (p->cfg.precision) {
         case BS_PREC_FP32:

@@ -1,0 +1,226 @@
+// Loaded window covariance from 16-bit windows on the tensor cores
+// (Eq. EmpiricalCov on the windowed vectors, plus loading), FP32 accumulate.
+//
+// With real rows m = 2w + c (c = 0: real part, 1: imaginary part of window
+// entry w) the K training vectors of a pair form a real 2W x K matrix A, and
+//   D = A A^T,   R_ij = (D[2i][2j] + D[2i+1][2j+1]
+//                        + j (D[2i+1][2j] - D[2i][2j+1])) / K.
+// One warp per pair computes the lower part of D with mma.sync m16n8k16
+// (FP16 or BF16 inputs, FP32 accumulators): per 16 vectors, two
+// ldmatrix.x4.trans per 16-row tile of A and per 16 columns of A^T, and one
+// MMA per (16 x 8) output tile on or below the diagonal.
+//
+// Windows stream through two per-warp shared-memory stages of 64 vectors
+// (cp.async, the next chunk loads while the current one is consumed); the
+// stage rows are 80 bytes apart so that ldmatrix's 8 row reads hit 8
+// different bank groups.  The accumulators are folded into double-float
+// every 128 vectors, and R is assembled in FP64.
+//
+// The covariance is HBM-bound (2 W flop per byte for 16-bit windows): the
+// tensor cores remove the FP32 multiply-add work that otherwise bounds the
+// kernel, leaving the window stream.
+#include "common.cuh"
+#include "internal.h"
+
+namespace bs {
+
+constexpr int MMA_CH = 64;                 // vectors per stage
+constexpr int MMA_RS = 40;                 // stage row stride in 16-bit elements (80 bytes)
+constexpr int MMA_WARPS = 4;               // warps (= pairs) per CTA
+
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_mma() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_mma() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+__device__ __forceinline__ void ldsm_x4_trans(unsigned (&r)[4], const void *row_addr) {
+    const unsigned a = static_cast<unsigned>(__cvta_generic_to_shared(row_addr));
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(a));
+}
+
+template <int PREC>
+__device__ __forceinline__ void mma16816(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
+    if constexpr (PREC == BS_PREC_FP16) {
+        asm volatile(
+            "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+            "{%0,%1,%2,%3};"
+            : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+            : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+    } else {
+        asm volatile(
+            "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+            "{%0,%1,%2,%3};"
+            : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+            : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+    }
+}
+
+__device__ __forceinline__ void df_fold(float &hi, float &lo, float b) {
+    const float s = hi + b;
+    const float bb = s - hi;
+    lo += (hi - (s - bb)) + (b - bb);
+    hi = s;
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(MMA_WARPS * 32)
+    window_cov_mma_kernel(const void *__restrict__ z, const int64_t *__restrict__ ztr_off,
+                          const int32_t *__restrict__ Wg, const int32_t *__restrict__ Kg,
+                          const int64_t *__restrict__ roff, const float *__restrict__ delta_pair, double delta,
+                          double inv_sc2, double2 *__restrict__ R, int64_t pairs) {
+    __shared__ __align__(16) uint16_t stage[MMA_WARPS][2][MMA_CH][MMA_RS];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t g = (int64_t)blockIdx.x * MMA_WARPS + warp;
+    if (g >= pairs) return;   // uniform per warp; no CTA-wide barrier below
+    uint16_t(*st)[MMA_CH][MMA_RS] = stage[warp];
+    const int W = Wg[g], K = Kg[g];
+    const int M2 = 2 * W;                       // real rows, <= 32
+    const int nmt = (M2 + 15) >> 4;             // 16-row tiles of A
+    const int nnt = (M2 + 7) >> 3;              // 8-column tiles of A^T
+    const uint32_t *zg = reinterpret_cast<const uint32_t *>(z) + ztr_off[g];   // one 32-bit word per complex
+
+    // zero both stages (padding rows / columns must read as 0)
+    for (int q = lane; q < 2 * MMA_CH * MMA_RS / 2; q += 32) reinterpret_cast<uint32_t *>(&st[0][0][0])[q] = 0u;
+    __syncwarp();
+
+    // lane -> (window entry w = lane % 16, vector parity lane / 16): no division
+    const int lw = lane & 15, lv = lane >> 4;
+    auto issue = [&](int k0, int buf) {
+        const int n = min(MMA_CH, K - k0);
+        if (lw < W) {
+            const uint32_t *src = zg + (int64_t)(k0 + lv) * W + lw;
+            for (int v = lv; v < n; v += 2, src += 2 * W) cp_async4(&st[buf][v][2 * lw], src);
+        }
+        cp_async_commit_mma();
+    };
+
+    float acc[2][4][4];
+    float hi[2][4][4], lo[2][4][4];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[a][b][e] = hi[a][b][e] = lo[a][b][e] = 0.f;
+
+    const int mi = lane >> 3, rr = lane & 7;   // ldmatrix: matrix index and row of this lane's address
+    issue(0, 0);
+    int buf = 0;
+    for (int k0 = 0; k0 < K; k0 += MMA_CH, buf ^= 1) {
+        const int n = min(MMA_CH, K - k0);
+        if (k0 + MMA_CH < K) {
+            issue(k0 + MMA_CH, buf ^ 1);
+            cp_async_wait_mma<1>();
+        } else {
+            cp_async_wait_mma<0>();
+        }
+        __syncwarp();
+        if (n < MMA_CH) {   // last chunk: vectors n .. up to the next multiple of 16 must be zero
+            const int top = (n + 15) & ~15;
+            for (int q = lane; q < (top - n) * MMA_RS / 2; q += 32)
+                reinterpret_cast<uint32_t *>(&st[buf][n][0])[q] = 0u;
+            __syncwarp();
+        }
+        for (int kk = 0; kk < n; kk += 16) {
+            // A^T fragments (B operand) for column tiles 0..nnt-1, two tiles per ldmatrix.x4
+            unsigned bfr[4][2];
+#pragma unroll
+            for (int tp = 0; tp < 2; ++tp) {
+                if (2 * tp < nnt) {
+                    // matrices: (cols 16tp, k), (16tp, k+8), (16tp+8, k), (16tp+8, k+8)
+                    const int col = 16 * tp + ((mi >> 1) << 3);
+                    const int krow = kk + ((mi & 1) << 3) + rr;
+                    unsigned r[4];
+                    ldsm_x4_trans(r, &st[buf][krow][col]);
+                    bfr[2 * tp][0] = r[0];
+                    bfr[2 * tp][1] = r[1];
+                    bfr[2 * tp + 1][0] = r[2];
+                    bfr[2 * tp + 1][1] = r[3];
+                }
+            }
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt) {
+                if (mt < nmt) {
+                    // matrices: (rows 16mt, k), (16mt+8, k), (16mt, k+8), (16mt+8, k+8)
+                    const int row = 16 * mt + ((mi & 1) << 3);
+                    const int krow = kk + ((mi >> 1) << 3) + rr;
+                    unsigned afr[4];
+                    ldsm_x4_trans(afr, &st[buf][krow][row]);
+#pragma unroll
+                    for (int nt = 0; nt < 4; ++nt)
+                        if (nt < nnt && 16 * mt + 15 >= 8 * nt) mma16816<PREC>(acc[mt][nt], afr, bfr[nt][0], bfr[nt][1]);
+                }
+            }
+        }
+        // fold the FP32 accumulators (at most 128 vectors each) into double-float
+        if ((k0 / MMA_CH) % 2 == 1 || k0 + MMA_CH >= K) {
+#pragma unroll
+            for (int a = 0; a < 2; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b)
+                    if (a < nmt && b < nnt && 16 * a + 15 >= 8 * b) {
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            df_fold(hi[a][b][e], lo[a][b][e], acc[a][b][e]);
+                            acc[a][b][e] = 0.f;
+                        }
+                    }
+        }
+        __syncwarp();   // this stage is reloaded two chunks later
+    }
+
+    // D (double) into the warp's stage area, then R from its 2x2 real blocks
+    double *Dm = reinterpret_cast<double *>(&st[0][0][0]);   // [32][32] doubles = 8 KB <= 10 KB
+    const int gr = lane >> 2, tg = lane & 3;
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt)
+            if (mt < nmt && nt < nnt && 16 * mt + 15 >= 8 * nt) {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int row = 16 * mt + gr + ((e >> 1) << 3);
+                    const int col = 8 * nt + 2 * tg + (e & 1);
+                    Dm[row * 32 + col] = (double)hi[mt][nt][e] + (double)lo[mt][nt][e];
+                }
+            }
+    __syncwarp();
+    const double sc = inv_sc2 / (double)K;
+    const double d = delta_pair ? (double)delta_pair[g] : delta;
+    double2 *Rg = R + roff[g];
+    const int E = W * (W + 1) / 2;
+    for (int e = lane; e < E; e += 32) {
+        int i = 0, r2 = e;
+        while (r2 > i) { r2 -= i + 1; ++i; }
+        const int j = r2;
+        const double re = (Dm[(2 * i) * 32 + 2 * j] + Dm[(2 * i + 1) * 32 + 2 * j + 1]) * sc;
+        const double im = (Dm[(2 * i + 1) * 32 + 2 * j] - Dm[(2 * i) * 32 + 2 * j + 1]) * sc;
+        if (i == j) {
+            Rg[i * W + i] = make_double2(re + d, 0.0);
+        } else {
+            Rg[i * W + j] = make_double2(re, im);
+            Rg[j * W + i] = make_double2(re, -im);
+        }
+    }
+}
+
+bs_status launch_window_cov_mma(const bs_plan *p, const void *ztr, const float *delta, double2 *R,
+                                cudaStream_t st) {
+    const int64_t G = p->pairs;
+    const unsigned blocks = (unsigned)((G + MMA_WARPS - 1) / MMA_WARPS);
+    const double sc = 1.0 / ((double)p->cfg.store_scale * (double)p->cfg.store_scale);
+    if (p->cfg.precision == BS_PREC_FP16)
+        window_cov_mma_kernel<BS_PREC_FP16><<<blocks, MMA_WARPS * 32, 0, st>>>(
+            ztr, p->d_ztr_off, p->d_Wg, p->d_Kg, p->d_roff, delta, p->cfg.delta, sc, R, G);
+    else
+        window_cov_mma_kernel<BS_PREC_BF16><<<blocks, MMA_WARPS * 32, 0, st>>>(
+            ztr, p->d_ztr_off, p->d_Wg, p->d_Kg, p->d_roff, delta, p->cfg.delta, sc, R, G);
+    return check_launch("covariance (tensor core) launch");
+}
+
+}  // namespace bs

@@ -293,3 +293,101 @@ def test_full_size_c3_sampled(precision):
     assert set(np.unique(res.info)).issubset({0, -2})
     worst, loss = check_end_to_end(cfg, sc, res, subbands=[0, 37, 64, 127])
     print(f"C3 prec={precision}: max weight rel err {worst:.2e}, max |SINR loss| {loss:.2e} dB")
+
+
+def uneven_small_config():
+    """C4-like: uneven W in {3,5,7,9,11,15} and K in [2W, 8W], scaled down."""
+    base = all_configs()["C4"]
+    rng = np.random.default_rng(5)
+    T = 24
+    W = tuple(int(w) for w in rng.choice([3, 5, 7, 9, 11, 15], size=T))
+    K = tuple(int(rng.integers(2 * w, 8 * w + 1)) for w in W)
+    return scaled_config(base, name="uneven-small", N=256, F=512, L=16, M=512, T=T, W=W, K=K,
+                         P_tr=8, P_te=2, n_jam=4)
+
+
+@pytest.mark.parametrize("precision", [P.BS_PREC_FP32, P.BS_PREC_FP16])
+def test_fused_cov_solve_matches_unfused(precision):
+    """bs_cov_solve (persistent, work queue) against bs_window_cov +
+    bs_mvdr_solve on the same windows, uneven W and K."""
+    cfg = uneven_small_config()
+    sc = make_scene(cfg)
+    out = {}
+    for flags in (0, P.BS_FLAG_FUSED):
+        res = run_gpu(cfg, sc.x, sc.u_tgt, precision=precision, flags=flags, keep_xc=False)
+        out[flags] = res
+    a, b = out[0], out[P.BS_FLAG_FUSED]
+    assert np.array_equal(a.z_train, b.z_train)
+    np.testing.assert_allclose(a.R, b.R, rtol=0, atol=1e-6 * np.abs(b.R).max())
+    # the two kernels sum in different orders: agreement within the sum of
+    # their errors against the oracle (each far below the 1e-3 target)
+    worst = 0.0
+    for g in range(a.plan.sizes.pairs):
+        pa, pb = a.pair(g), b.pair(g)
+        assert pa["info"] == pb["info"]
+        worst = max(worst, rel(pa["c"], pb["c"]))
+    print(f"fused vs unfused (prec {precision}): max weight difference {worst:.2e}")
+    assert worst <= 2e-4
+
+
+def test_uneven_end_to_end():
+    cfg = uneven_small_config()
+    sc = make_scene(cfg)
+    res = run_gpu(cfg, sc.x, sc.u_tgt, flags=P.BS_FLAG_FUSED, keep_xc=False)
+    worst, loss = check_end_to_end(cfg, sc, res)
+    print(f"uneven-small FP32: max weight rel err {worst:.2e}, max |SINR loss| {loss:.2e} dB")
+
+
+def test_full_size_c4_sampled():
+    """The batched-uneven workload at full size (N=1024, 256 targets, W in
+    {3..15}, K in [2W, 8W], 32768 pairs) through bs_run with the fused
+    persistent kernel; the oracle checks 2 subbands x 256 targets."""
+    cfg = all_configs()["C4"]
+    sc = make_scene(cfg)
+    res = run_gpu(cfg, sc.x, sc.u_tgt, flags=P.BS_FLAG_FUSED, keep_xc=False)
+    assert set(np.unique(res.info)).issubset({0, -2})
+    worst, loss = check_end_to_end(cfg, sc, res, subbands=[5, 100])
+    print(f"C4 FP32: max weight rel err {worst:.2e}, max |SINR loss| {loss:.2e} dB")
+
+
+def test_graph_and_autotune():
+    """The autotuner picks a launch shape; a captured CUDA graph of the whole
+    pass then reproduces bs_run (same shape) bit for bit."""
+    cfg = uneven_small_config()
+    sc = make_scene(cfg)
+    plan = P.Plan.from_scene_config(cfg, sc.u_tgt, flags=P.BS_FLAG_FUSED)
+    b = P.alloc_buffers(plan)
+    b.x.copy_(torch.from_numpy(sc.x.reshape(-1)))
+    st = torch.cuda.Stream()
+    tuned = P.bs_autotune(plan, b, stream=st)
+    assert tuned["threads"] in (64, 128) and 1 <= tuned["ctas_per_sm"] <= 8 and tuned["ms"] > 0
+    P.bs_run(plan, b, stream=st)
+    st.synchronize()
+    ref_out, ref_c = b.out.clone(), b.c.clone()
+    b.out.zero_(); b.c.zero_()
+    g = P.Graph(plan, b, st)
+    for _ in range(3):
+        g.launch(st)
+    st.synchronize()
+    assert torch.equal(b.out, ref_out)
+    assert torch.equal(b.c, ref_c)
+    assert plan.device_status() == 0
+
+
+@pytest.mark.parametrize("precision", [P.BS_PREC_FP16, P.BS_PREC_BF16])
+def test_tensor_core_covariance(precision):
+    """16-bit windows: the tensor-core covariance equals the FP64 covariance
+    of the same (dequantised) windows to COV_TOL, for W = 1..16 and K not a
+    multiple of 16 (ragged last k-block)."""
+    base = all_configs()["C1"]
+    W = (1, 2, 3, 5, 8, 9, 12, 15, 16)
+    K = (1, 7, 17, 40, 64, 65, 100, 127, 128)
+    cfg = scaled_config(base, name="tc-cov", N=64, F=512, L=4, M=64, T=len(W), W=W, K=K,
+                        P_tr=1, P_te=1, n_jam=2)
+    sc = make_scene(cfg)
+    res = run_gpu(cfg, sc.x, sc.u_tgt, precision=precision, keep_xc=False)
+    for g in range(res.plan.sizes.pairs):
+        pr = res.pair(g)
+        Ro = O.window_covariance(pr["z_train"].astype(np.complex128), cfg.delta)
+        assert np.abs(pr["R"] - Ro).max() <= COV_TOL * np.abs(Ro).max(), (g, np.abs(pr["R"] - Ro).max())
+        np.testing.assert_allclose(pr["R"], pr["R"].conj().T, atol=0)
