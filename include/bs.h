@@ -231,6 +231,36 @@ bs_status bs_autotune(bs_plan *plan, const void *z_train, bs_cf64 *R, bs_cf32 *c
 /* Sets the launch shape of bs_cov_solve (threads 64 or 128; 1..32 CTAs per SM). */
 bs_status bs_set_launch(bs_plan *plan, int32_t threads, int32_t ctas_per_sm);
 
+/* Allocation-free covariance + solve.  The paper has no counterpart: this
+ * is a service for callers that may not allocate device memory while they
+ * run (a real-time processing loop whose memory is fixed at start-up, where
+ * an allocation could stall the device; a host application that owns all
+ * device buffers and forbids libraries to allocate).  Such callers cannot
+ * create a bs_plan (plan creation allocates), so every per-pair table is
+ * passed in, as device arrays of `pairs` entries:
+ *   W, K        window size (1..16) and training-vector count (>= 1);
+ *   ztr_off     element offset of the pair's K x W training windows in
+ *               z_train (as bs_plan_offsets' ztr_off);
+ *   woff        offset of the pair's W values in a_hi, a_lo, a_fp64 and c;
+ *   a_hi, a_lo  windowed steering vectors as FP32 high and low parts
+ *               (hi = (float)a, lo = (float)(a - hi)); a_fp64 the same in FP64.
+ * Results are those of bs_cov_solve (R is not produced): c, info; a pair
+ * whose W or K is out of range gets info = -3 and its c is not written.
+ * This call allocates nothing: its scratch (queue head and cost-ordered pair
+ * list) is a fixed array in device memory with room for 262144 pairs, held
+ * by every GPU that loads the library until the process exits; larger
+ * `pairs` are refused with BS_EINVAL.  The first call on a device looks up
+ * that array's device address (cudaGetSymbolAddress) and caches it, so make
+ * the first call on each device before any stream capture.  All calls share
+ * the array: calls whose kernels could overlap on the GPU (other streams,
+ * other host threads on the same device) race and must not be issued; each
+ * call rewrites the parts it uses, so earlier contents do no harm. */
+bs_status bs_cov_solve_noalloc(const void *z_train, int32_t precision, float store_scale,
+                               const int32_t *W, const int32_t *K, const int64_t *ztr_off,
+                               const int64_t *woff, const bs_cf32 *a_hi, const bs_cf32 *a_lo,
+                               const bs_cf64 *a_fp64, int64_t pairs, double delta, double kappa_max,
+                               uint32_t flags, bs_cf32 *c, int32_t *info, bs_stream stream);
+
 /* Beamformer output (Sec. II-B): out[g][v'] = c_g^H z_test[g][v'], v' < Vte. */
 bs_status bs_apply(const bs_plan *plan, const bs_cf32 *z_test, const bs_cf32 *c,
                    bs_cf32 *out, bs_stream stream);

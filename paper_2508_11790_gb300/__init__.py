@@ -20,7 +20,7 @@ from .build import lib_path
 __all__ = [
     "BS_PREC_FP32", "BS_PREC_FP16", "BS_PREC_BF16",
     "BS_FLAG_PLAIN", "BS_FLAG_NO_REFINE", "BS_FLAG_NO_FP64", "BS_FLAG_NO_TMA", "BS_FLAG_FUSED", "BS_FLAG_SIMT_COV",
-    "bs_cov_solve", "bs_autotune", "bs_set_launch", "Graph",
+    "bs_cov_solve", "bs_autotune", "bs_set_launch", "Graph", "bs_cov_solve_noalloc",
     "BsError", "Plan", "Buffers", "alloc_buffers", "lib", "bs_plan_tables_host",
     "bs_channelize", "bs_beamspace", "bs_beamspace_full", "bs_window_cov",
     "bs_mvdr_solve", "bs_apply", "bs_run", "bs_run_host",
@@ -80,6 +80,8 @@ _SIGS = {
     "bs_cov_solve": ([_P, _P, _P, _P, _P, _P, _P], ctypes.c_int),
     "bs_autotune": ([_P, _P, _P, _P, _P, _P, _P, _P, _P], ctypes.c_int),
     "bs_set_launch": ([_P, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
+    "bs_cov_solve_noalloc": ([_P, ctypes.c_int32, ctypes.c_float, _P, _P, _P, _P, _P, _P, _P, ctypes.c_int64,
+                              ctypes.c_double, ctypes.c_double, ctypes.c_uint32, _P, _P, _P], ctypes.c_int),
     "bs_graph_create": ([_P, ctypes.POINTER(_Buffers), _P, ctypes.POINTER(_P)], ctypes.c_int),
     "bs_graph_launch": ([_P, _P], ctypes.c_int),
     "bs_graph_destroy": ([_P], None),
@@ -334,6 +336,25 @@ def bs_cov_solve(plan: Plan, z_train: torch.Tensor, c: torch.Tensor, info: torch
                               _ptr(R, torch.complex128, s.r_elems, "R"),
                               _ptr(c, torch.complex64, s.c_elems, "c"),
                               _ptr(info, torch.int32, s.pairs, "info"), _stream(stream)), "bs_cov_solve")
+
+
+def bs_cov_solve_noalloc(z_train: torch.Tensor, precision: int, W: torch.Tensor, K: torch.Tensor,
+                         ztr_off: torch.Tensor, woff: torch.Tensor, a_hi: torch.Tensor, a_lo: torch.Tensor,
+                         a_fp64: torch.Tensor, delta: float, c: torch.Tensor, info: torch.Tensor,
+                         store_scale: float = 1.0, kappa_max: float = 0.0, flags: int = 0, stream=None):
+    """Allocation-free covariance + solve (no plan): every per-pair table is a
+    caller-provided device tensor; see bs_cov_solve_noalloc in include/bs.h."""
+    pairs = W.numel()
+    zt = torch.complex64 if precision == BS_PREC_FP32 else (
+        torch.float16 if precision == BS_PREC_FP16 else torch.bfloat16)
+    _check(lib().bs_cov_solve_noalloc(
+        _ptr(z_train, zt, None, "z_train"), precision, store_scale,
+        _ptr(W, torch.int32, pairs, "W"), _ptr(K, torch.int32, pairs, "K"),
+        _ptr(ztr_off, torch.int64, pairs, "ztr_off"), _ptr(woff, torch.int64, pairs, "woff"),
+        _ptr(a_hi, torch.complex64, None, "a_hi"), _ptr(a_lo, torch.complex64, None, "a_lo"),
+        _ptr(a_fp64, torch.complex128, None, "a_fp64"), pairs, delta, kappa_max, flags,
+        _ptr(c, torch.complex64, None, "c"), _ptr(info, torch.int32, pairs, "info"), _stream(stream)),
+        "bs_cov_solve_noalloc")
 
 
 def bs_autotune(plan: Plan, bufs: "Buffers", stream=None) -> dict:

@@ -243,4 +243,42 @@ bs_status launch_cov_solve(const bs_plan *p, const void *ztr, const float *delta
     }
 }
 
+// Launch of the fused kernel from explicit per-pair device tables (no plan),
+// for the allocation-free entry point.  `order` / `head` point into the
+// caller's scratch; R is not produced.
+bs_status launch_cov_solve_tables(const void *z, int precision, float store_scale, const int32_t *Wg,
+                                  const int32_t *Kg, const int64_t *ztr_off, const int64_t *woff,
+                                  const float2 *at32, const float2 *atlo, const double2 *at64,
+                                  const int32_t *order, int64_t pairs, double delta, double kappa_max,
+                                  uint32_t flags, float2 *c, int32_t *info, int *head, int grid,
+                                  cudaStream_t st) {
+    CovSolveArgs a;
+    a.z = z;
+    a.ztr_off = ztr_off;
+    a.Wg = Wg;
+    a.Kg = Kg;
+    a.woff = woff;
+    a.roff = nullptr;
+    a.at32 = at32;
+    a.atlo = atlo;
+    a.at64 = at64;
+    a.order = order;
+    a.pairs = pairs;
+    a.delta_pair = nullptr;
+    a.delta = delta;
+    a.inv_sc = 1.0f / store_scale;
+    a.kappa_max = kappa_max;
+    a.refine = (flags & BS_FLAG_NO_REFINE) ? 0 : 1;
+    a.allow_f64 = (flags & BS_FLAG_NO_FP64) ? 0 : 1;
+    a.c = c;
+    a.info = info;
+    a.R = nullptr;
+    a.head = head;
+    switch (precision) {
+        case BS_PREC_FP32: return launch_cs_prec<BS_PREC_FP32>(nullptr, a, 128, grid, st);
+        case BS_PREC_FP16: return launch_cs_prec<BS_PREC_FP16>(nullptr, a, 128, grid, st);
+        default: return launch_cs_prec<BS_PREC_BF16>(nullptr, a, 128, grid, st);
+    }
+}
+
 }  // namespace bs

@@ -69,6 +69,12 @@ bs_status launch_apply(const bs_plan *p, const float2 *zte, const float2 *c, flo
                        cudaStream_t st);
 bs_status launch_cov_solve(const bs_plan *p, const void *ztr, const float *delta, double2 *R, float2 *c,
                            int32_t *info, int *head, const CovSolveLaunch &cfg, cudaStream_t st);
+bs_status launch_cov_solve_tables(const void *z, int precision, float store_scale, const int32_t *Wg,
+                                  const int32_t *Kg, const int64_t *ztr_off, const int64_t *woff,
+                                  const float2 *at32, const float2 *atlo, const double2 *at64,
+                                  const int32_t *order, int64_t pairs, double delta, double kappa_max,
+                                  uint32_t flags, float2 *c, int32_t *info, int *head, int grid,
+                                  cudaStream_t st);
 int beamspace_vectors_per_cta(int M);
 
 }  // namespace bs
