@@ -221,14 +221,15 @@ bs_status bs_mvdr_solve(const bs_plan *plan, const bs_cf64 *R, bs_cf32 *c, int32
 bs_status bs_cov_solve(const bs_plan *plan, const void *z_train, const float *delta_pair, bs_cf64 *R,
                        bs_cf32 *c, int32_t *info, bs_stream stream);
 
-/* Times bs_cov_solve for every launch shape (64 or 128 threads per CTA; 2,
- * 3, 4, 5, 6 or 8 CTAs per SM) on the caller's buffers (3 runs each, after
- * one warm-up), keeps the fastest in the plan and returns it (any output
- * pointer may be NULL).  Synchronises `stream`; overwrites R, c, info. */
+/* Times bs_cov_solve for every launch shape (128 threads per CTA; 1, 2, 3,
+ * 4, 5, 6 or 8 persistent CTAs per SM) on the caller's buffers (3 runs each,
+ * after one warm-up), keeps the fastest in the plan and returns it (any
+ * output pointer may be NULL).  Synchronises `stream`; overwrites R, c,
+ * info. */
 bs_status bs_autotune(bs_plan *plan, const void *z_train, bs_cf64 *R, bs_cf32 *c, int32_t *info,
                       bs_stream stream, int32_t *threads, int32_t *ctas_per_sm, float *ms);
 
-/* Sets the launch shape of bs_cov_solve (threads 64 or 128; 1..32 CTAs per SM). */
+/* Sets the launch shape of bs_cov_solve (threads 128; 1..32 CTAs per SM). */
 bs_status bs_set_launch(bs_plan *plan, int32_t threads, int32_t ctas_per_sm);
 
 /* Allocation-free covariance + solve.  The paper has no counterpart: this

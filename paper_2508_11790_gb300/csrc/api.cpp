@@ -144,16 +144,16 @@ bs_status bs_autotune(bs_plan *p, const void *z_train, bs_cf64 *R, bs_cf32 *c, i
     BS_REQUIRE(p && z_train && c && info, "NULL argument");
     if (bs_status s = check_device(p)) return s;
     const cudaStream_t st = (cudaStream_t)stream;
-    const int thr[2] = {64, 128};
-    const int cps[6] = {2, 3, 4, 5, 6, 8};
+    const int thr[1] = {128};
+    const int cps[7] = {1, 2, 3, 4, 5, 6, 8};
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         return bs::cuda_error(cudaGetLastError(), "event create");
     bs::CovSolveLaunch best = p->cs;
     float best_ms = 1e30f;
     bs_status s = BS_OK;
-    for (int ti = 0; ti < 2 && !s; ++ti) {
-        for (int ci = 0; ci < 6 && !s; ++ci) {
+    for (int ti = 0; ti < 1 && !s; ++ti) {
+        for (int ci = 0; ci < 7 && !s; ++ci) {
             bs::CovSolveLaunch cand;
             cand.threads = thr[ti];
             cand.ctas_per_sm = cps[ci];
@@ -187,7 +187,7 @@ bs_status bs_autotune(bs_plan *p, const void *z_train, bs_cf64 *R, bs_cf32 *c, i
 
 bs_status bs_set_launch(bs_plan *p, int32_t threads, int32_t ctas_per_sm) {
     BS_REQUIRE(p, "NULL plan");
-    BS_REQUIRE(threads == 64 || threads == 128, "threads must be 64 or 128");
+    BS_REQUIRE(threads == 128, "threads must be 128");
     BS_REQUIRE(ctas_per_sm >= 1 && ctas_per_sm <= 32, "ctas_per_sm must be in 1..32");
     p->cs.threads = threads;
     p->cs.ctas_per_sm = ctas_per_sm;

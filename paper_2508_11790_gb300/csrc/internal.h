@@ -12,7 +12,7 @@
 namespace bs {
 // Launch shape of the fused covariance + solve kernel (set by bs_autotune).
 struct CovSolveLaunch {
-    int threads = 128;      // 64 or 128
+    int threads = 128;      // threads per CTA (128)
     int ctas_per_sm = 5;
 };
 }  // namespace bs

@@ -83,7 +83,7 @@ __device__ __forceinline__ float hw_sumf(unsigned mask, float x) {
 
 // Whole solve in FP64 for one pair (escalation path), row `lane` of R given
 // in D.  Returns 0 or pivot+1.
-static __device__ int solve_f64_rows(unsigned mask, int lane, int W, double2 (&D)[WMAX], double2 a,
+static __device__ __forceinline__ int solve_f64_rows(unsigned mask, int lane, int W, double2 (&D)[WMAX], double2 a,
                                      double2 (*Ld)[WMAX + 1], double2 &c_out) {
     const bool row = lane < W;
 #pragma unroll
@@ -153,7 +153,8 @@ static __device__ int solve_f64_rows(unsigned mask, int lane, int W, double2 (&D
     return 0;
 }
 
-static __device__ int solve_f64(unsigned mask, int lane, int W, const double2 *__restrict__ Rg, double2 a,
+// Not inlined: compiled once per translation unit for every window size.
+static __device__ __noinline__ int solve_f64(unsigned mask, int lane, int W, const double2 *__restrict__ Rg, double2 a,
                                 double2 (*Ld)[WMAX + 1], double2 &c_out) {
     double2 D[WMAX];
     const bool row = lane < W;
@@ -202,20 +203,24 @@ __device__ __forceinline__ float2 residual_df(unsigned mask, int lane, Rows rows
     return make_float2(sr + cr, si + ci);
 }
 
-// Solve one pair with the calling half-warp (lanes 0..15 of `mask`).
-// Row loader: rows(j) returns entry (lane, j) of R as FP32 (hi, lo) parts in
-// a float4 {hi.re, hi.im, lo.re, lo.im}; Rg64 (may be NULL) is the FP64
-// matrix for the escalation path (else the escalation reads hi + lo).
-// a32/alo: the windowed steering vector as hi / lo FP32 parts, a64 in FP64
-// (escalation).  scratch: [16][17] double2 per half-warp.  Writes c[0..W)
-// and *info.
-template <int WT, class Rows>
-__device__ __forceinline__ void solve_pair_rows(unsigned mask, int lane, Rows rows,
-                                                const float2 *__restrict__ a32g, const float2 *__restrict__ alog,
-                                                const double2 *__restrict__ a64g, float2 *__restrict__ c,
-                                                int32_t *__restrict__ info, double kappa_max, int refine,
-                                                int allow_f64, double2 (*scratch)[WMAX + 1],
-                                                const double2 *Rg64) {
+// Solve one pair of window size WT with the calling half-warp (lanes 0..15
+// of `mask`).  Rg: its W x W covariance in FP64 (row-major; global or shared
+// memory), read as FP32 (hi, lo) parts; a32/alo: the windowed steering
+// vector as hi / lo FP32 parts, a64 in FP64 (escalation).  scratch: [16][17]
+// double2 per half-warp.  Writes c[0..W) and *info.  Not inlined, so each
+// window size is compiled once per translation unit.
+template <int WT>
+static __device__ __noinline__ void solve_pair_fixed(unsigned mask, int lane, const double2 *Rg,
+                                                     const float2 *__restrict__ a32g,
+                                                     const float2 *__restrict__ alog,
+                                                     const double2 *__restrict__ a64g, float2 *__restrict__ c,
+                                                     int32_t *__restrict__ info, double kappa_max, int refine,
+                                                     int allow_f64, double2 (*scratch)[WMAX + 1]) {
+    auto rows = [&](int j) -> float4 {
+        const double2 r = Rg[lane * WT + j];
+        const float hx = (float)r.x, hy = (float)r.y;
+        return make_float4(hx, hy, (float)(r.x - (double)hx), (float)(r.y - (double)hy));
+    };
     float2(*Lsf)[WMAX + 1] = reinterpret_cast<float2(*)[WMAX + 1]>(&scratch[0][0]);
     constexpr int W = WT;
     const bool row = lane < W;
@@ -285,24 +290,12 @@ __device__ __forceinline__ void solve_pair_rows(unsigned mask, int lane, Rows ro
         if (lane == 0) *info = fail;
         return;
     }
-    // FP64 path: the matrix in FP64 (given, or rebuilt from hi + lo)
+    // FP64 path
     double2(*Ldd)[WMAX + 1] = scratch;
     __syncwarp(mask);
     double2 cd;
     const double2 a64 = row ? a64g[lane] : make_double2(0.0, 0.0);
-    int f64fail;
-    if (Rg64) {
-        f64fail = solve_f64(mask, lane, W, Rg64, a64, Ldd, cd);
-    } else {
-        // rebuild row `lane` from hi + lo
-        double2 rowbuf[WMAX];
-#pragma unroll
-        for (int j = 0; j < WMAX; ++j) {
-            const float4 r4 = (row && j < W) ? rows(j < W ? j : 0) : make_float4(0.f, 0.f, 0.f, 0.f);
-            rowbuf[j] = make_double2((double)r4.x + (double)r4.z, (double)r4.y + (double)r4.w);
-        }
-        f64fail = solve_f64_rows(mask, lane, W, rowbuf, a64, Ldd, cd);
-    }
+    const int f64fail = solve_f64(mask, lane, W, Rg, a64, Ldd, cd);
     if (f64fail) {
         if (row) c[lane] = make_float2(nanf(""), nanf(""));
         if (lane == 0) *info = f64fail;
@@ -312,20 +305,15 @@ __device__ __forceinline__ void solve_pair_rows(unsigned mask, int lane, Rows ro
     if (lane == 0) *info = -2;
 }
 
-// Convenience: R stored as FP64 (global or shared memory); dispatches on W
-// to the solve compiled for that window size.
+// R stored as FP64 (global or shared memory); dispatches on W to the solve
+// compiled for that window size.
 __device__ __forceinline__ void solve_pair(unsigned mask, int lane, int W, const double2 *Rg,
                                            const float2 *__restrict__ a32g, const float2 *__restrict__ alog,
                                            const double2 *__restrict__ a64g, float2 *__restrict__ c,
                                            int32_t *__restrict__ info, double kappa_max, int refine,
                                            int allow_f64, double2 (*scratch)[WMAX + 1]) {
-    auto rows = [&](int j) -> float4 {
-        const double2 r = Rg[lane * W + j];
-        const float hx = (float)r.x, hy = (float)r.y;
-        return make_float4(hx, hy, (float)(r.x - (double)hx), (float)(r.y - (double)hy));
-    };
 #define BS_SOLVE_CASE(n) \
-    case n: solve_pair_rows<n>(mask, lane, rows, a32g, alog, a64g, c, info, kappa_max, refine, allow_f64, scratch, Rg); break;
+    case n: solve_pair_fixed<n>(mask, lane, Rg, a32g, alog, a64g, c, info, kappa_max, refine, allow_f64, scratch); break;
     switch (W) {
         BS_SOLVE_CASE(1) BS_SOLVE_CASE(2) BS_SOLVE_CASE(3) BS_SOLVE_CASE(4)
         BS_SOLVE_CASE(5) BS_SOLVE_CASE(6) BS_SOLVE_CASE(7) BS_SOLVE_CASE(8)
