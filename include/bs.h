@@ -285,6 +285,82 @@ bs_status bs_graph_create(const bs_plan *plan, const bs_buffers *buf, bs_stream 
 bs_status bs_graph_launch(bs_graph *graph, bs_stream stream);
 void      bs_graph_destroy(bs_graph *graph);
 
+/* ---------------------------------------------------- learned loading --- */
+/* A small MLP predicts, from a window's covariance estimated with few
+ * training vectors (K = 2W), the diagonal loading delta and a diagonal
+ * preconditioner d of the MVDR solve.  The paper loads nothing and learns
+ * nothing (Eq. BeamCorrMVDR is solved as is); this follows the workload's
+ * learned-loading direction, with plain MVDR at a fixed delta as fallback
+ * and SINR judge.  Layers: n_in -> n_hidden -> n_hidden -> n_out, ReLU
+ * between, y = [log10 delta, log10 d_1 .. log10 d_W]. */
+
+/* Parameters (all device memory, caller-owned, P = bs_mlp_param_count()
+ * floats each, layout W1 [H][n_in] | b1 [H] | W2 [H][H] | b2 [H] |
+ * W3 [n_out][H] | b3 [n_out]).  master: FP32 parameters (Adam updates these);
+ * weights_bf16: BF16 copy read by the forward and backward products (FP32
+ * accumulation); grad, adam_m, adam_v: FP32.  step counts Adam updates. */
+typedef struct {
+    int32_t n_in, n_hidden, n_out;
+    int32_t step;
+    float *master;
+    void *weights_bf16;
+    float *grad, *adam_m, *adam_v;
+} bs_mlp;
+
+/* Activations of one batch (device, caller-owned): z1, h1, z2, h2, dh1, dh2
+ * [capacity][n_hidden]; y, dy [capacity][n_out]. */
+typedef struct {
+    int64_t capacity;
+    float *z1, *h1, *z2, *h2;
+    float *y, *dy;
+    float *dh1, *dh2;
+} bs_mlp_work;
+
+int64_t   bs_mlp_param_count(int32_t n_in, int32_t n_hidden, int32_t n_out);
+
+/* Features of every pair (plan with one window size W for all targets) from
+ * its unloaded covariance R (bs_window_cov with zero loading): with
+ * tau = tr(R)/W, [diag(R)/tau | Re R_ij/tau (i > j, row-major) | Im R_ij/tau |
+ * Re a~/|a~| | Im a~/|a~| | log10 tau | log10(K/W)], W^2 + 2W + 2 floats per
+ * pair, X: [pairs][W^2 + 2W + 2]. */
+bs_status bs_features(const bs_plan *plan, const bs_cf64 *R_unloaded, float *X, bs_stream stream);
+
+/* Output SINR of each pair's weights against a reference covariance:
+ * sinr[g] = |c^H a~|^2 / (c^H R_ref c) (FP64). */
+bs_status bs_output_sinr(const bs_plan *plan, const bs_cf32 *c, const bs_cf64 *R_ref, double *sinr,
+                         bs_stream stream);
+
+/* Training targets: for each pair, the loading grid[k] of largest
+ * sinr[k][pair] (first on ties), T[pair] = [log10 delta*,
+ * -0.5 log10(R_ii + delta*)] (nout = 1 + W), best_delta (may be NULL). */
+bs_status bs_loading_labels(const bs_plan *plan, const double *sinr, int32_t ngrid, const double *grid,
+                            const bs_cf64 *R_unloaded, int32_t nout, float *T, float *best_delta,
+                            bs_stream stream);
+
+/* Forward pass: Y [batch][n_out] from X [batch][n_in] (batch <= capacity). */
+bs_status bs_mlp_forward(const bs_mlp *mlp, const float *X, int64_t batch, float *Y, const bs_mlp_work *work,
+                         bs_stream stream);
+
+/* One training step on a batch: forward (into work->y), mean-squared-error
+ * gradient against T [batch][n_out] (loss, if not NULL, is incremented by the
+ * batch loss, FP64 device scalar), backward, and an Adam update (lr > 0;
+ * beta 0.9 / 0.999, eps 1e-8, bias-corrected) of master with a fresh BF16
+ * copy.  lr = 0 stops after the gradients (left in mlp->grad). */
+bs_status bs_mlp_train_step(bs_mlp *mlp, const float *X, const float *T, int64_t batch, const bs_mlp_work *work,
+                            float lr, double *loss, bs_stream stream);
+
+/* Refresh the BF16 weight copy from master. */
+bs_status bs_mlp_sync_bf16(const bs_mlp *mlp, bs_stream stream);
+
+/* dst[r] = src[idx[r]] for rows of `cols` floats (minibatch assembly). */
+bs_status bs_gather_rows(const float *src, const int64_t *idx, int64_t rows, int32_t cols, float *dst,
+                         bs_stream stream);
+
+/* delta[g] = 10^Y[g][0] clipped to [lo, hi]; non-finite -> fallback.  The
+ * result feeds bs_window_cov's per-pair loading. */
+bs_status bs_loading_from_mlp(const float *Y, int32_t nout, int64_t pairs, float lo, float hi, float fallback,
+                              float *delta, bs_stream stream);
+
 /* ------------------------------------------------------------- errors --- */
 const char *bs_status_string(bs_status s);
 const char *bs_last_error(void);   /* thread-local text of the last error */

@@ -1,0 +1,287 @@
+"""Learned diagonal loading: binding of the MLP entry points, training-data
+pipeline and training loop.
+
+All arithmetic runs in the library's kernels (features, SINR judge, labels,
+MLP forward / backward / Adam, minibatch gather); torch only allocates
+device memory and the host only draws shuffling permutations and the
+initial weights.
+
+Training data (one scene at a time): two plans over the same raw records
+share the channelised cube: one with the few-snapshot training count
+K = 2W (the features and the candidate weights) and one with K_ref >> K
+(the reference covariance that judges the output SINR).  For every loading
+on a 61-point grid (0.1 .. 1e4, noise-variance units) the few-snapshot
+weights are solved and judged; the label is the best loading and the
+diagonal preconditioner it implies.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+import torch
+
+from . import (BS_PREC_FP32, BsError, Plan, _P, _check, _ptr, _stream, lib)
+
+LOADING_GRID = 10.0 ** np.linspace(-1.0, 4.0, 61)
+
+
+class _Mlp(ctypes.Structure):
+    _fields_ = [("n_in", ctypes.c_int32), ("n_hidden", ctypes.c_int32), ("n_out", ctypes.c_int32),
+                ("step", ctypes.c_int32), ("master", ctypes.c_void_p), ("weights_bf16", ctypes.c_void_p),
+                ("grad", ctypes.c_void_p), ("adam_m", ctypes.c_void_p), ("adam_v", ctypes.c_void_p)]
+
+
+class _Work(ctypes.Structure):
+    _fields_ = [("capacity", ctypes.c_int64)] + [(n, ctypes.c_void_p) for n in
+                                                 ("z1", "h1", "z2", "h2", "y", "dy", "dh1", "dh2")]
+
+
+_SIGS = {
+    "bs_mlp_param_count": ([ctypes.c_int32] * 3, ctypes.c_int64),
+    "bs_features": ([_P, _P, _P, _P], ctypes.c_int),
+    "bs_output_sinr": ([_P, _P, _P, _P, _P], ctypes.c_int),
+    "bs_loading_labels": ([_P, _P, ctypes.c_int32, _P, _P, ctypes.c_int32, _P, _P, _P], ctypes.c_int),
+    "bs_mlp_forward": ([ctypes.POINTER(_Mlp), _P, ctypes.c_int64, _P, ctypes.POINTER(_Work), _P], ctypes.c_int),
+    "bs_mlp_train_step": ([ctypes.POINTER(_Mlp), _P, _P, ctypes.c_int64, ctypes.POINTER(_Work), ctypes.c_float, _P,
+                           _P], ctypes.c_int),
+    "bs_mlp_sync_bf16": ([ctypes.POINTER(_Mlp), _P], ctypes.c_int),
+    "bs_gather_rows": ([_P, _P, ctypes.c_int64, ctypes.c_int32, _P, _P], ctypes.c_int),
+    "bs_loading_from_mlp": ([_P, ctypes.c_int32, ctypes.c_int64, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                             _P, _P], ctypes.c_int),
+}
+_bound = False
+
+
+def _lib():
+    global _bound
+    L = lib()
+    if not _bound:
+        for name, (args, res) in _SIGS.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _bound = True
+    return L
+
+
+def feature_count(W: int) -> int:
+    return W * W + 2 * W + 2
+
+
+def he_uniform_params(n_in: int, n_hidden: int, n_out: int, seed: int) -> np.ndarray:
+    """Flat FP32 parameter vector in the library's layout, He-uniform weights
+    (bound sqrt(6 / fan_in)) and zero biases, drawn in the order W1, W2, W3."""
+    g = np.random.default_rng(seed)
+    parts = []
+    for fo, fi in ((n_hidden, n_in), (n_hidden, n_hidden), (n_out, n_hidden)):
+        b = np.sqrt(6.0 / fi)
+        parts += [g.uniform(-b, b, size=(fo, fi)).ravel(), np.zeros(fo)]
+    return np.concatenate(parts).astype(np.float32)
+
+
+def unflatten(p: np.ndarray, n_in: int, n_hidden: int, n_out: int) -> dict:
+    """Flat vector -> {W1, b1, W2, b2, W3, b3} (views, float64 copies)."""
+    out, o = {}, 0
+    for k, shape in (("W1", (n_hidden, n_in)), ("b1", (n_hidden,)), ("W2", (n_hidden, n_hidden)),
+                     ("b2", (n_hidden,)), ("W3", (n_out, n_hidden)), ("b3", (n_out,))):
+        n = int(np.prod(shape))
+        out[k] = np.asarray(p[o:o + n], dtype=np.float64).reshape(shape)
+        o += n
+    return out
+
+
+class LoadingMLP:
+    """The MLP's device buffers and its C entry points."""
+
+    def __init__(self, n_in: int, n_out: int, n_hidden: int = 256, capacity: int = 4096, seed: int = 1,
+                 device="cuda", params: Optional[np.ndarray] = None):
+        L = _lib()
+        self.n_in, self.n_hidden, self.n_out, self.capacity = n_in, n_hidden, n_out, capacity
+        P = int(L.bs_mlp_param_count(n_in, n_hidden, n_out))
+        self.P = P
+        init = he_uniform_params(n_in, n_hidden, n_out, seed) if params is None else params.astype(np.float32)
+        if init.size != P:
+            raise BsError("parameter vector has the wrong size")
+        f32 = dict(dtype=torch.float32, device=device)
+        self.master = torch.from_numpy(init).to(device)
+        self.bf16 = torch.empty(P, dtype=torch.bfloat16, device=device)
+        self.grad = torch.zeros(P, **f32)
+        self.m = torch.zeros(P, **f32)
+        self.v = torch.zeros(P, **f32)
+        self.work = {k: torch.empty(capacity * (n_out if k in ("y", "dy") else n_hidden), **f32)
+                     for k in ("z1", "h1", "z2", "h2", "y", "dy", "dh1", "dh2")}
+        self.loss = torch.zeros(1, dtype=torch.float64, device=device)
+        self._m = _Mlp(n_in, n_hidden, n_out, 0, self.master.data_ptr(), self.bf16.data_ptr(),
+                       self.grad.data_ptr(), self.m.data_ptr(), self.v.data_ptr())
+        self._w = _Work(capacity, *[self.work[k].data_ptr() for k in
+                                    ("z1", "h1", "z2", "h2", "y", "dy", "dh1", "dh2")])
+        _check(L.bs_mlp_sync_bf16(ctypes.byref(self._m), _stream(None)), "bs_mlp_sync_bf16")
+
+    @property
+    def step(self) -> int:
+        return self._m.step
+
+    def forward(self, X: torch.Tensor, batch: int, Y: torch.Tensor, stream=None):
+        _check(_lib().bs_mlp_forward(ctypes.byref(self._m), _ptr(X, torch.float32, batch * self.n_in, "X"), batch,
+                                     _ptr(Y, torch.float32, batch * self.n_out, "Y"), ctypes.byref(self._w),
+                                     _stream(stream)), "bs_mlp_forward")
+
+    def train_step(self, X: torch.Tensor, T: torch.Tensor, batch: int, lr: float, stream=None):
+        _check(_lib().bs_mlp_train_step(ctypes.byref(self._m), _ptr(X, torch.float32, batch * self.n_in, "X"),
+                                        _ptr(T, torch.float32, batch * self.n_out, "T"), batch,
+                                        ctypes.byref(self._w), lr, self.loss.data_ptr(), _stream(stream)),
+               "bs_mlp_train_step")
+
+    def predict(self, X: torch.Tensor, n: int, stream=None) -> torch.Tensor:
+        """Network outputs [n][n_out] for feature rows X (chunks of capacity)."""
+        Y = torch.empty(n * self.n_out, dtype=torch.float32, device=X.device)
+        for s in range(0, n, self.capacity):
+            b = min(self.capacity, n - s)
+            self.forward(X[s * self.n_in:], b, Y[s * self.n_out:], stream)
+        return Y
+
+    def loading(self, Y: torch.Tensor, n: int, lo=0.1, hi=1e4, fallback=10.0, stream=None) -> torch.Tensor:
+        d = torch.empty(n, dtype=torch.float32, device=Y.device)
+        _check(_lib().bs_loading_from_mlp(_ptr(Y, torch.float32, n * self.n_out, "Y"), self.n_out, n, lo, hi,
+                                          fallback, d.data_ptr(), _stream(stream)), "bs_loading_from_mlp")
+        return d
+
+
+@dataclass
+class WindowData:
+    X: torch.Tensor            # [n][n_in] features
+    T: torch.Tensor            # [n][n_out] targets
+    sinr: torch.Tensor         # [ngrid][n] SINR of each grid loading (reference covariance)
+    best: torch.Tensor         # [n] grid loading of the label
+    n: int
+
+
+def scene_windows(cfg, x: np.ndarray, u, K_small: int, grid=LOADING_GRID, device="cuda") -> WindowData:
+    """Features, labels and the SINR of every grid loading for all pairs of
+    one scene.  cfg must give every target the same W; its P_tr records give
+    the reference covariance (K_ref = P_tr * B vectors)."""
+    from . import (alloc_buffers, bs_beamspace, bs_channelize, bs_mvdr_solve, bs_window_cov)
+    W = int(cfg.W[0])
+    T = cfg.T
+    B = cfg.F // cfg.L
+    K_ref = cfg.P_tr * B
+    common = dict(N=cfg.N, F=cfg.F, L=cfg.L, M=cfg.M, u=u, W=[W] * T, P_train=cfg.P_tr, P_test=cfg.P_te,
+                  fc=cfg.fc, fs=cfg.fs, fd=cfg.fd, delta=cfg.delta, precision=BS_PREC_FP32)
+    ps = Plan(K=[K_small] * T, **common)
+    pr = Plan(K=[K_ref] * T, **common)
+    bs_ = alloc_buffers(ps, device)
+    ztr_r = torch.empty(pr.sizes.ztrain_elems, dtype=torch.complex64, device=device)
+    Rr = torch.empty(pr.sizes.r_elems, dtype=torch.complex128, device=device)
+    bs_.x.copy_(torch.from_numpy(np.ascontiguousarray(x).reshape(-1)))
+    G = ps.sizes.pairs
+    zeros = torch.zeros(G, dtype=torch.float32, device=device)
+    bs_channelize(ps, bs_.x, bs_.xc)
+    bs_beamspace(ps, bs_.xc, bs_.z_train, bs_.z_test)
+    bs_beamspace(pr, bs_.xc, ztr_r, bs_.z_test)
+    Rs = torch.empty_like(bs_.R)
+    bs_window_cov(ps, bs_.z_train, Rs, delta_pair=zeros)
+    bs_window_cov(pr, ztr_r, Rr, delta_pair=zeros)
+    L = _lib()
+    nin, nout = feature_count(W), 1 + W
+    X = torch.empty(G * nin, dtype=torch.float32, device=device)
+    _check(L.bs_features(ps.handle, Rs.data_ptr(), X.data_ptr(), _stream(None)), "bs_features")
+    sinr = torch.empty(len(grid) * G, dtype=torch.float64, device=device)
+    dl = torch.empty(G, dtype=torch.float32, device=device)
+    for k, d in enumerate(grid):
+        dl.fill_(float(d))
+        bs_window_cov(ps, bs_.z_train, bs_.R, delta_pair=dl)
+        bs_mvdr_solve(ps, bs_.R, bs_.c, bs_.info)
+        _check(L.bs_output_sinr(ps.handle, bs_.c.data_ptr(), Rr.data_ptr(), sinr[k * G:].data_ptr(),
+                                _stream(None)), "bs_output_sinr")
+    gd = torch.from_numpy(np.asarray(grid, dtype=np.float64)).to(device)
+    Tt = torch.empty(G * nout, dtype=torch.float32, device=device)
+    best = torch.empty(G, dtype=torch.float32, device=device)
+    _check(L.bs_loading_labels(ps.handle, sinr.data_ptr(), len(grid), gd.data_ptr(), Rs.data_ptr(), nout,
+                               Tt.data_ptr(), best.data_ptr(), _stream(None)), "bs_loading_labels")
+    torch.cuda.synchronize()
+    return WindowData(X, Tt, sinr.view(len(grid), G), best, G)
+
+
+def concat(parts) -> WindowData:
+    return WindowData(torch.cat([p.X for p in parts]), torch.cat([p.T for p in parts]),
+                      torch.cat([p.sinr for p in parts], dim=1), torch.cat([p.best for p in parts]),
+                      sum(p.n for p in parts))
+
+
+def train(mlp: LoadingMLP, data: WindowData, epochs: int, batch: int, lr: float, seed: int = 0,
+          stream=None) -> list:
+    """Adam over shuffled minibatches; returns the mean loss of every epoch."""
+    g = np.random.default_rng(seed)
+    dev = data.X.device
+    xb = torch.empty(batch * mlp.n_in, dtype=torch.float32, device=dev)
+    tb = torch.empty(batch * mlp.n_out, dtype=torch.float32, device=dev)
+    L = _lib()
+    hist = []
+    for _ in range(epochs):
+        perm = torch.from_numpy(g.permutation(data.n).astype(np.int64)).to(dev)
+        mlp.loss.zero_()
+        nb = 0
+        for s in range(0, data.n - batch + 1, batch):
+            idx = perm[s:s + batch]
+            _check(L.bs_gather_rows(data.X.data_ptr(), idx.data_ptr(), batch, mlp.n_in, xb.data_ptr(),
+                                    _stream(stream)), "bs_gather_rows")
+            _check(L.bs_gather_rows(data.T.data_ptr(), idx.data_ptr(), batch, mlp.n_out, tb.data_ptr(),
+                                    _stream(stream)), "bs_gather_rows")
+            mlp.train_step(xb, tb, batch, lr, stream)
+            nb += 1
+        torch.cuda.synchronize()
+        hist.append(float(mlp.loss.item()) / max(nb, 1))
+    return hist
+
+
+def grid_sinr_at(data: WindowData, delta: float) -> torch.Tensor:
+    """SINR of the grid loading nearest to delta (per pair)."""
+    k = int(np.argmin(np.abs(np.log10(LOADING_GRID) - np.log10(delta))))
+    return data.sinr[k]
+
+
+def evaluate_scene(cfg, x: np.ndarray, u, K_small: int, mlp: LoadingMLP, base_delta: float = 10.0,
+                   device="cuda") -> dict:
+    """Runs the path on one scene with the network's per-pair loading and with
+    the fixed loading base_delta; both weight sets are judged by the output
+    SINR against the reference covariance (K_ref = P_tr * B vectors).
+    Returns per-pair SINRs (numpy) and the mean gain in dB."""
+    from . import (alloc_buffers, bs_beamspace, bs_channelize, bs_mvdr_solve, bs_window_cov)
+    W = int(cfg.W[0])
+    T = cfg.T
+    B = cfg.F // cfg.L
+    common = dict(N=cfg.N, F=cfg.F, L=cfg.L, M=cfg.M, u=u, W=[W] * T, P_train=cfg.P_tr, P_test=cfg.P_te,
+                  fc=cfg.fc, fs=cfg.fs, fd=cfg.fd, delta=base_delta, precision=BS_PREC_FP32)
+    ps = Plan(K=[K_small] * T, **common)
+    pr = Plan(K=[cfg.P_tr * B] * T, **common)
+    b = alloc_buffers(ps, device)
+    ztr_r = torch.empty(pr.sizes.ztrain_elems, dtype=torch.complex64, device=device)
+    Rr = torch.empty(pr.sizes.r_elems, dtype=torch.complex128, device=device)
+    b.x.copy_(torch.from_numpy(np.ascontiguousarray(x).reshape(-1)))
+    G = ps.sizes.pairs
+    zeros = torch.zeros(G, dtype=torch.float32, device=device)
+    bs_channelize(ps, b.x, b.xc)
+    bs_beamspace(ps, b.xc, b.z_train, b.z_test)
+    bs_beamspace(pr, b.xc, ztr_r, b.z_test)
+    bs_window_cov(pr, ztr_r, Rr, delta_pair=zeros)
+    L = _lib()
+    Ru = torch.empty_like(b.R)
+    bs_window_cov(ps, b.z_train, Ru, delta_pair=zeros)
+    X = torch.empty(G * feature_count(W), dtype=torch.float32, device=device)
+    _check(L.bs_features(ps.handle, Ru.data_ptr(), X.data_ptr(), _stream(None)), "bs_features")
+    Y = mlp.predict(X, G)
+    dhat = mlp.loading(Y, G, fallback=base_delta)
+    out = {}
+    for name, dpair in (("learned", dhat), ("fixed", None)):
+        bs_window_cov(ps, b.z_train, b.R, delta_pair=dpair)
+        bs_mvdr_solve(ps, b.R, b.c, b.info)
+        s = torch.empty(G, dtype=torch.float64, device=device)
+        _check(L.bs_output_sinr(ps.handle, b.c.data_ptr(), Rr.data_ptr(), s.data_ptr(), _stream(None)),
+               "bs_output_sinr")
+        out[name] = s.cpu().numpy()
+    out["delta_hat"] = dhat.cpu().numpy()
+    out["gain_db"] = float(np.mean(10.0 * np.log10(out["learned"] / out["fixed"])))
+    return out
