@@ -7,71 +7,10 @@
 // variant then writes, for every target, the W_t beams of its window
 // (start_g + w mod M) straight from shared memory into the packed training
 // or test window arrays; the full variant writes all M beams.
-#include "common.cuh"
+#include "beamspace_dev.cuh"
 #include "internal.h"
 
 namespace bs {
-
-// Vectors per CTA: vpb = 4096 / M clamped to [1, 16] (34.8 KB of padded
-// shared memory at M = 2048), 256 threads, one radix-16 butterfly per thread
-// per pass, so that four CTAs (32 warps) share an SM.
-template <int M>
-struct BsCfg {
-    static constexpr int vpb = (4096 / M > 16) ? 16 : ((4096 / M < 1) ? 1 : 4096 / M);
-    static constexpr int nthr = (vpb * M / 16 < 256) ? vpb * M / 16 : 256;
-    static constexpr int pl = padded_len(M);
-    static constexpr size_t smem = (size_t)vpb * pl * sizeof(float2);
-    static constexpr int minb = (smem <= 40 * 1024) ? 4 : ((smem <= 72 * 1024) ? 3 : 1);
-};
-
-struct GatherArgs {
-    int64_t nvec;           // vectors = P * F
-    int log2F, log2B, L, P_train, T;
-    int uniform;            // B % vpb == 0: the vectors of a CTA share (record, subband)
-    const int32_t *gather;  // [vpb * sumW] (t << 8) | (c << 4) | w
-    int ngather;
-    const int32_t *Wg, *Kg, *start;
-    const int64_t *ztr_off, *zte_off;
-    void *ztr;              // training windows (plan precision)
-    float2 *zte;            // test windows
-    float store_scale;
-};
-
-template <int PREC>
-__device__ __forceinline__ void store_train(void *z, int64_t idx, float2 v, float sc) {
-    if constexpr (PREC == BS_PREC_FP32) {
-        reinterpret_cast<float2 *>(z)[idx] = v;
-    } else if constexpr (PREC == BS_PREC_FP16) {
-        reinterpret_cast<__half2 *>(z)[idx] = __floats2half2_rn(v.x * sc, v.y * sc);
-    } else {
-        reinterpret_cast<__nv_bfloat162 *>(z)[idx] = __floats2bfloat162_rn(v.x * sc, v.y * sc);
-    }
-}
-
-constexpr int kTabT = 256;   // targets whose gather entries are staged in shared memory
-
-// Gather entry of target t for a CTA at subband s whose first vector is v0:
-// base element offset in the window array, start | (W << 16), output count.
-__device__ __forceinline__ void fill_target_entry(const GatherArgs &ga, int t, int s, int v0, int nv,
-                                                  bool train, long long *base, int *sw, int *nout,
-                                                  int slot = -1) {
-    const int i = slot < 0 ? t : slot;
-    const int64_t g = (int64_t)t * ga.L + s;
-    const int W = __ldg(&ga.Wg[g]);
-    const int st = __ldg(&ga.start[g]);
-    int n = nv * W;
-    long long b;
-    if (train) {
-        const int K = __ldg(&ga.Kg[g]);
-        n = (v0 >= K) ? 0 : min(n, (K - v0) * W);
-        b = __ldg(&ga.ztr_off[g]) + (long long)v0 * W;
-    } else {
-        b = __ldg(&ga.zte_off[g]) + (long long)v0 * W;
-    }
-    base[i] = b;
-    sw[i] = st | (W << 16);
-    nout[i] = n;
-}
 
 // kFull: write all M beams to out[v][m]; else gather windows (PREC = storage
 // precision of the training windows).
@@ -250,6 +189,9 @@ bs_status launch_beamspace(const bs_plan *p, const float2 *xc, void *ztr, float2
     ga.ztr = ztr;
     ga.zte = zte;
     ga.store_scale = p->cfg.store_scale;
+    bool used = false;
+    const bs_status s = launch_beamspace_tma(p, xc, ga, st, &used);
+    if (s || used) return s;
     switch (p->cfg.precision) {
         case BS_PREC_FP32: return launch_bs<false, BS_PREC_FP32>(p->cfg.M, xc, ga.nvec, p->cfg.N, p->d_twM, nullptr, ga, st);
         case BS_PREC_FP16: return launch_bs<false, BS_PREC_FP16>(p->cfg.M, xc, ga.nvec, p->cfg.N, p->d_twM, nullptr, ga, st);
