@@ -10,10 +10,13 @@
 // ldmatrix.x4.trans per 16-row tile of A and per 16 columns of A^T, and one
 // MMA per (16 x 8) output tile on or below the diagonal.
 //
-// Windows stream through two per-warp shared-memory stages of 64 vectors
-// (cp.async, the next chunk loads while the current one is consumed); the
-// stage rows are 80 bytes apart so that ldmatrix's 8 row reads hit 8
-// different bank groups.  The accumulators are folded into double-float
+// Windows stream through a per-warp ring of shared-memory stages of 64
+// vectors (cp.async).  For 2W <= 24 the stage rows are 48 bytes apart
+// (ldmatrix's 8 row reads then start in 8 different 16-byte bank groups)
+// and the ring has 4 stages, so three chunks are in flight while one is
+// consumed; wider windows use 80-byte rows and 2 stages in the same 12 KB.
+// A window stream of one pair is latency-bound per warp: the bytes in flight
+// per SM set its bandwidth.  The accumulators are folded into double-float
 // every 128 vectors, and R is assembled in FP64.
 //
 // The covariance is HBM-bound (2 W flop per byte for 16-bit windows): the
@@ -25,8 +28,12 @@
 namespace bs {
 
 constexpr int MMA_CH = 64;                 // vectors per stage
-constexpr int MMA_RS = 40;                 // stage row stride in 16-bit elements (80 bytes)
 constexpr int MMA_WARPS = 4;               // warps (= pairs) per CTA
+constexpr int MMA_WARP_HALVES = 6144;      // per-warp ring: 4 x 64 x 24 or 2 x 64 x 40 16-bit elements (12 KB)
+// dynamic shared memory: the rings plus 64 bytes, because ldmatrix of the
+// columns 16..31 of a 24-element row reads into the next row (those columns
+// only feed rows and columns of D beyond 2W, which are not used)
+constexpr size_t MMA_SMEM = (size_t)MMA_WARPS * MMA_WARP_HALVES * 2 + 64;
 
 __device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
     const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
@@ -67,34 +74,62 @@ __device__ __forceinline__ void df_fold(float &hi, float &lo, float b) {
     hi = s;
 }
 
+// Double-float values (h + l, |l| <= ulp(h)/2) for the epilogue: GB300's
+// FP64 pipe is narrow, so R is assembled in FP32 pairs and only the final
+// value of each entry is converted to FP64.
+struct DF {
+    float h, l;
+};
+__device__ __forceinline__ DF df_norm(float h, float l) {   // |l| small against h
+    const float s = h + l;
+    return DF{s, l - (s - h)};
+}
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+    const float s = a.h + b.h;
+    const float bb = s - a.h;
+    const float e = (a.h - (s - bb)) + (b.h - bb) + a.l + b.l;
+    return df_norm(s, e);
+}
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+    const float p = a.h * b.h;
+    float e = fmaf(a.h, b.h, -p);
+    e = fmaf(a.h, b.l, e);
+    e = fmaf(a.l, b.h, e);
+    return df_norm(p, e);
+}
+__device__ __forceinline__ double df_to_double(DF a) { return (double)a.h + (double)a.l; }
+
 template <int PREC>
 __global__ void __launch_bounds__(MMA_WARPS * 32)
     window_cov_mma_kernel(const void *__restrict__ z, const int64_t *__restrict__ ztr_off,
                           const int32_t *__restrict__ Wg, const int32_t *__restrict__ Kg,
-                          const int64_t *__restrict__ roff, const float *__restrict__ delta_pair, double delta,
-                          double inv_sc2, double2 *__restrict__ R, int64_t pairs) {
-    __shared__ __align__(16) uint16_t stage[MMA_WARPS][2][MMA_CH][MMA_RS];
+                          const int64_t *__restrict__ roff, const float *__restrict__ delta_pair, DF delta,
+                          DF inv_sc2, double2 *__restrict__ R, int64_t pairs) {
+    extern __shared__ __align__(16) uint16_t mma_smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t g = (int64_t)blockIdx.x * MMA_WARPS + warp;
     if (g >= pairs) return;   // uniform per warp; no CTA-wide barrier below
-    uint16_t(*st)[MMA_CH][MMA_RS] = stage[warp];
+    uint16_t *ring = mma_smem + warp * MMA_WARP_HALVES;
     const int W = Wg[g], K = Kg[g];
     const int M2 = 2 * W;                       // real rows, <= 32
+    const int RS = (M2 <= 24) ? 24 : 40;        // stage row stride (16-bit elements)
+    const int nst = (M2 <= 24) ? 4 : 2;         // stages in the ring
+    auto srow = [&](int b, int v) { return ring + (b * MMA_CH + v) * RS; };
     const int nmt = (M2 + 15) >> 4;             // 16-row tiles of A
     const int nnt = (M2 + 7) >> 3;              // 8-column tiles of A^T
     const uint32_t *zg = reinterpret_cast<const uint32_t *>(z) + ztr_off[g];   // one 32-bit word per complex
 
-    // zero both stages (padding rows / columns must read as 0)
-    for (int q = lane; q < 2 * MMA_CH * MMA_RS / 2; q += 32) reinterpret_cast<uint32_t *>(&st[0][0][0])[q] = 0u;
+    // zero the ring (padding columns must read as 0)
+    for (int q = lane; q < MMA_WARP_HALVES / 2; q += 32) reinterpret_cast<uint32_t *>(ring)[q] = 0u;
     __syncwarp();
 
     // lane -> (window entry w = lane % 16, vector parity lane / 16): no division
     const int lw = lane & 15, lv = lane >> 4;
-    auto issue = [&](int k0, int buf) {
+    auto issue = [&](int k0, int buf) {   // commits one group, empty past the end
         const int n = min(MMA_CH, K - k0);
         if (lw < W) {
             const uint32_t *src = zg + (int64_t)(k0 + lv) * W + lw;
-            for (int v = lv; v < n; v += 2, src += 2 * W) cp_async4(&st[buf][v][2 * lw], src);
+            for (int v = lv; v < n; v += 2, src += 2 * W) cp_async4(srow(buf, v) + 2 * lw, src);
         }
         cp_async_commit_mma();
     };
@@ -109,21 +144,19 @@ __global__ void __launch_bounds__(MMA_WARPS * 32)
             for (int e = 0; e < 4; ++e) acc[a][b][e] = hi[a][b][e] = lo[a][b][e] = 0.f;
 
     const int mi = lane >> 3, rr = lane & 7;   // ldmatrix: matrix index and row of this lane's address
-    issue(0, 0);
-    int buf = 0;
-    for (int k0 = 0; k0 < K; k0 += MMA_CH, buf ^= 1) {
+    const int nch = (K + MMA_CH - 1) / MMA_CH;
+    for (int c = 0; c < nst - 1; ++c) issue(c * MMA_CH, c);
+    for (int c = 0; c < nch; ++c) {
+        const int k0 = c * MMA_CH, buf = c % nst;
         const int n = min(MMA_CH, K - k0);
-        if (k0 + MMA_CH < K) {
-            issue(k0 + MMA_CH, buf ^ 1);
-            cp_async_wait_mma<1>();
-        } else {
-            cp_async_wait_mma<0>();
-        }
+        issue(k0 + (nst - 1) * MMA_CH, (c + nst - 1) % nst);   // stage consumed at c - 1
+        if (nst == 4) cp_async_wait_mma<3>();
+        else cp_async_wait_mma<1>();
         __syncwarp();
         if (n < MMA_CH) {   // last chunk: vectors n .. up to the next multiple of 16 must be zero
             const int top = (n + 15) & ~15;
-            for (int q = lane; q < (top - n) * MMA_RS / 2; q += 32)
-                reinterpret_cast<uint32_t *>(&st[buf][n][0])[q] = 0u;
+            for (int q = lane; q < (top - n) * RS / 2; q += 32)
+                reinterpret_cast<uint32_t *>(srow(buf, n))[q] = 0u;
             __syncwarp();
         }
         for (int kk = 0; kk < n; kk += 16) {
@@ -136,7 +169,7 @@ __global__ void __launch_bounds__(MMA_WARPS * 32)
                     const int col = 16 * tp + ((mi >> 1) << 3);
                     const int krow = kk + ((mi & 1) << 3) + rr;
                     unsigned r[4];
-                    ldsm_x4_trans(r, &st[buf][krow][col]);
+                    ldsm_x4_trans(r, srow(buf, krow) + col);
                     bfr[2 * tp][0] = r[0];
                     bfr[2 * tp][1] = r[1];
                     bfr[2 * tp + 1][0] = r[2];
@@ -150,7 +183,7 @@ __global__ void __launch_bounds__(MMA_WARPS * 32)
                     const int row = 16 * mt + ((mi & 1) << 3);
                     const int krow = kk + ((mi >> 1) << 3) + rr;
                     unsigned afr[4];
-                    ldsm_x4_trans(afr, &st[buf][krow][row]);
+                    ldsm_x4_trans(afr, srow(buf, krow) + row);
 #pragma unroll
                     for (int nt = 0; nt < 4; ++nt)
                         if (nt < nnt && 16 * mt + 15 >= 8 * nt) mma16816<PREC>(acc[mt][nt], afr, bfr[nt][0], bfr[nt][1]);
@@ -158,7 +191,7 @@ __global__ void __launch_bounds__(MMA_WARPS * 32)
             }
         }
         // fold the FP32 accumulators (at most 128 vectors each) into double-float
-        if ((k0 / MMA_CH) % 2 == 1 || k0 + MMA_CH >= K) {
+        if (c % 2 == 1 || c == nch - 1) {
 #pragma unroll
             for (int a = 0; a < 2; ++a)
 #pragma unroll
@@ -171,11 +204,13 @@ __global__ void __launch_bounds__(MMA_WARPS * 32)
                         }
                     }
         }
-        __syncwarp();   // this stage is reloaded two chunks later
+        __syncwarp();   // this stage is reloaded by the next iteration's issue
     }
+    cp_async_wait_mma<0>();   // the empty trailing groups
+    __syncwarp();
 
-    // D (double) into the warp's stage area, then R from its 2x2 real blocks
-    double *Dm = reinterpret_cast<double *>(&st[0][0][0]);   // [32][32] doubles = 8 KB <= 10 KB
+    // D (double-float) into the warp's ring, then R from its 2x2 real blocks
+    float2 *Dm = reinterpret_cast<float2 *>(ring);   // [32][32] pairs = 8 KB <= 12 KB
     const int gr = lane >> 2, tg = lane & 3;
 #pragma unroll
     for (int mt = 0; mt < 2; ++mt)
@@ -186,40 +221,66 @@ __global__ void __launch_bounds__(MMA_WARPS * 32)
                 for (int e = 0; e < 4; ++e) {
                     const int row = 16 * mt + gr + ((e >> 1) << 3);
                     const int col = 8 * nt + 2 * tg + (e & 1);
-                    Dm[row * 32 + col] = (double)hi[mt][nt][e] + (double)lo[mt][nt][e];
+                    Dm[row * 32 + col] = make_float2(hi[mt][nt][e], lo[mt][nt][e]);
                 }
             }
     __syncwarp();
-    const double sc = inv_sc2 / (double)K;
-    const double d = delta_pair ? (double)delta_pair[g] : delta;
+    // sc = inv_sc2 / K in double-float (K < 2^24 is exact in FP32)
+    const float Kf = (float)K;
+    const float q = inv_sc2.h / Kf;
+    const float rem = fmaf(-q, Kf, inv_sc2.h);
+    const DF sc = df_norm(q, (rem + inv_sc2.l) / Kf);
+    const DF dl = delta_pair ? DF{delta_pair[g], 0.f} : delta;
+    auto D = [&](int r, int c) {
+        const float2 v = Dm[r * 32 + c];
+        return DF{v.x, v.y};
+    };
     double2 *Rg = R + roff[g];
     const int E = W * (W + 1) / 2;
     for (int e = lane; e < E; e += 32) {
         int i = 0, r2 = e;
         while (r2 > i) { r2 -= i + 1; ++i; }
         const int j = r2;
-        const double re = (Dm[(2 * i) * 32 + 2 * j] + Dm[(2 * i + 1) * 32 + 2 * j + 1]) * sc;
-        const double im = (Dm[(2 * i + 1) * 32 + 2 * j] - Dm[(2 * i) * 32 + 2 * j + 1]) * sc;
+        DF re = df_mul(df_add(D(2 * i, 2 * j), D(2 * i + 1, 2 * j + 1)), sc);
         if (i == j) {
-            Rg[i * W + i] = make_double2(re + d, 0.0);
+            Rg[i * W + i] = make_double2(df_to_double(df_add(re, dl)), 0.0);
         } else {
-            Rg[i * W + j] = make_double2(re, im);
-            Rg[j * W + i] = make_double2(re, -im);
+            const DF nd = D(2 * i, 2 * j + 1);
+            const DF im = df_mul(df_add(D(2 * i + 1, 2 * j), DF{-nd.h, -nd.l}), sc);
+            const double rd = df_to_double(re), id = df_to_double(im);
+            Rg[i * W + j] = make_double2(rd, id);
+            Rg[j * W + i] = make_double2(rd, __longlong_as_double(__double_as_longlong(id) ^ (1ll << 63)));
         }
     }
+}
+
+static DF split_df(double v) {
+    const float h = (float)v;
+    return DF{h, (float)(v - (double)h)};
 }
 
 bs_status launch_window_cov_mma(const bs_plan *p, const void *ztr, const float *delta, double2 *R,
                                 cudaStream_t st) {
     const int64_t G = p->pairs;
     const unsigned blocks = (unsigned)((G + MMA_WARPS - 1) / MMA_WARPS);
-    const double sc = 1.0 / ((double)p->cfg.store_scale * (double)p->cfg.store_scale);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(window_cov_mma_kernel<BS_PREC_FP16>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MMA_SMEM);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(window_cov_mma_kernel<BS_PREC_BF16>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MMA_SMEM);
+        if (e != cudaSuccess) return cuda_error(e, "covariance (tensor core) attribute");
+        attr_set = true;
+    }
+    const DF sc = split_df(1.0 / ((double)p->cfg.store_scale * (double)p->cfg.store_scale));
+    const DF dl = split_df(p->cfg.delta);
     if (p->cfg.precision == BS_PREC_FP16)
-        window_cov_mma_kernel<BS_PREC_FP16><<<blocks, MMA_WARPS * 32, 0, st>>>(
-            ztr, p->d_ztr_off, p->d_Wg, p->d_Kg, p->d_roff, delta, p->cfg.delta, sc, R, G);
+        window_cov_mma_kernel<BS_PREC_FP16><<<blocks, MMA_WARPS * 32, MMA_SMEM, st>>>(
+            ztr, p->d_ztr_off, p->d_Wg, p->d_Kg, p->d_roff, delta, dl, sc, R, G);
     else
-        window_cov_mma_kernel<BS_PREC_BF16><<<blocks, MMA_WARPS * 32, 0, st>>>(
-            ztr, p->d_ztr_off, p->d_Wg, p->d_Kg, p->d_roff, delta, p->cfg.delta, sc, R, G);
+        window_cov_mma_kernel<BS_PREC_BF16><<<blocks, MMA_WARPS * 32, MMA_SMEM, st>>>(
+            ztr, p->d_ztr_off, p->d_Wg, p->d_Kg, p->d_roff, delta, dl, sc, R, G);
     return check_launch("covariance (tensor core) launch");
 }
 

@@ -391,3 +391,21 @@ def test_tensor_core_covariance(precision):
         Ro = O.window_covariance(pr["z_train"].astype(np.complex128), cfg.delta)
         assert np.abs(pr["R"] - Ro).max() <= COV_TOL * np.abs(Ro).max(), (g, np.abs(pr["R"] - Ro).max())
         np.testing.assert_allclose(pr["R"], pr["R"].conj().T, atol=0)
+
+
+@pytest.mark.parametrize("precision", [P.BS_PREC_FP16, P.BS_PREC_BF16])
+def test_tensor_core_covariance_long_streams(precision):
+    """K of several hundred vectors: the per-warp ring of window stages wraps
+    several times (4 stages of 48-byte rows for 2W <= 24, 2 stages of
+    80-byte rows above), with ragged last chunks."""
+    base = all_configs()["C1"]
+    W = (9, 12, 13, 16, 3)
+    K = (1000, 513, 300, 257, 640)
+    cfg = scaled_config(base, name="tc-cov-long", N=64, F=512, L=4, M=64, T=len(W), W=W, K=K,
+                        P_te=1, n_jam=2)
+    sc = make_scene(cfg)
+    res = run_gpu(cfg, sc.x, sc.u_tgt, precision=precision, keep_xc=False)
+    for g in range(res.plan.sizes.pairs):
+        pr = res.pair(g)
+        Ro = O.window_covariance(pr["z_train"].astype(np.complex128), cfg.delta)
+        assert np.abs(pr["R"] - Ro).max() <= COV_TOL * np.abs(Ro).max(), (g, np.abs(pr["R"] - Ro).max())
