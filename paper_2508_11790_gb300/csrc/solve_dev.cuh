@@ -203,6 +203,31 @@ __device__ __forceinline__ float2 residual_df(unsigned mask, int lane, Rows rows
     return make_float2(sr + cr, si + ci);
 }
 
+// Split a double into FP32 parts hi + lo (hi: the double rounded half-up to
+// 24 significant bits, lo: the rest rounded to FP32) with integer operations
+// only: GB300's FP64 pipe is narrow, and the conversions this replaces
+// ((float)d, d - (double)hi, (float)(...)) all ran on it.  Non-finite input
+// and magnitudes at or above 2^128 give an infinite or NaN hi; magnitudes
+// below 2^-126 give zero.
+__device__ __forceinline__ float2 split_f64(double d) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+    const unsigned hw = (unsigned)(b >> 32), lw = (unsigned)b;
+    const unsigned sign = hw & 0x80000000u;
+    const int e11 = (int)((hw >> 20) & 0x7FFu);
+    if (e11 == 0x7FF) return make_float2(__uint_as_float(sign | 0x7F800000u | (((hw & 0xFFFFFu) | lw) ? 0x400000u : 0u)), 0.f);
+    const int e8 = e11 - 896;   // FP32 biased exponent
+    if (e8 <= 0) return make_float2(0.f, 0.f);
+    if (e8 >= 255) return make_float2(__uint_as_float(sign | 0x7F800000u), 0.f);
+    const unsigned m23 = ((hw & 0xFFFFFu) << 3) | (lw >> 29);
+    const unsigned rest = lw & 0x1FFFFFFFu;   // 29 mantissa bits below hi
+    const unsigned up = rest >> 28;
+    const unsigned hb = (sign | ((unsigned)e8 << 23) | m23) + up;   // a carry moves into the exponent
+    const int lo_int = (int)rest - (int)(up << 29);               // d - hi in units of 2^(e11 - 1075)
+    const int el = e11 - 948;                                       // FP32 biased exponent of 2^(e11 - 1075)
+    const float lo = (el >= 1) ? (float)lo_int * __uint_as_float((unsigned)el << 23) : 0.f;
+    return make_float2(__uint_as_float(hb), sign ? -lo : lo);
+}
+
 // Solve one pair of window size WT with the calling half-warp (lanes 0..15
 // of `mask`).  Rg: its W x W covariance in FP64 (row-major; global or shared
 // memory), read as FP32 (hi, lo) parts; a32/alo: the windowed steering
@@ -218,8 +243,8 @@ static __device__ __noinline__ void solve_pair_fixed(unsigned mask, int lane, co
                                                      int allow_f64, double2 (*scratch)[WMAX + 1]) {
     auto rows = [&](int j) -> float4 {
         const double2 r = Rg[lane * WT + j];
-        const float hx = (float)r.x, hy = (float)r.y;
-        return make_float4(hx, hy, (float)(r.x - (double)hx), (float)(r.y - (double)hy));
+        const float2 x = split_f64(r.x), y = split_f64(r.y);
+        return make_float4(x.x, y.x, x.y, y.y);
     };
     float2(*Lsf)[WMAX + 1] = reinterpret_cast<float2(*)[WMAX + 1]>(&scratch[0][0]);
     constexpr int W = WT;
@@ -263,7 +288,7 @@ static __device__ __noinline__ void solve_pair_fixed(unsigned mask, int lane, co
         }
     }
     const float ratio = dmax / dmin;
-    const bool escalate = allow_f64 && (fail != 0 || (double)ratio * (double)ratio > kappa_max);
+    const bool escalate = allow_f64 && (fail != 0 || ratio * ratio > (float)kappa_max);
     if (!escalate && fail == 0) {
 #pragma unroll
         for (int j = 0; j < WT; ++j)

@@ -256,6 +256,32 @@ def test_solve_info_codes():
     assert np.isnan(c[off["woff"][3]:off["woff"][4]]).all()
 
 
+def test_solve_scale_invariance_and_split_edges():
+    """MVDR weights do not change when R is scaled (Eq. BeamCorrMVDR): the
+    solve reads its FP64 covariance through an integer-operation hi/lo split,
+    so scales 2^-40 .. 2^40 (the FP32 solve's range: a^H R^-1 a is squared in
+    FP32), entries whose low mantissa bits round the high part up into the
+    next binade, and an infinite entry (info -1) are checked against the
+    oracle."""
+    rng = np.random.default_rng(17)
+    W = 7
+    Q, _ = np.linalg.qr(rng.standard_normal((W, W)) + 1j * rng.standard_normal((W, W)))
+    base = (Q * np.linspace(1.0, 30.0, W)) @ Q.conj().T
+    # diagonal 2^24 - 2^-29 ... : the FP32 high part rounds up to a power of two
+    edge = base.copy()
+    edge[np.arange(W), np.arange(W)] += 2.0 ** 24 - 2.0 ** -28 - np.real(np.diag(base)).max()
+    scales = [2.0 ** -40, 2.0 ** -17, 1.0, 3.0 ** 20, 2.0 ** 35, 2.0 ** 40]
+    inf = base.copy(); inf[1, 1] = np.inf
+    Rs = [base * sc_ for sc_ in scales] + [edge, inf]
+    off, c, info = _solve_only(Rs, None)
+    assert list(info[:-1]) == [0] * (len(Rs) - 1) and info[-1] == -1
+    at = off["a_tilde"]
+    for g in range(len(Rs) - 1):
+        a = at[off["woff"][g]:off["woff"][g + 1]]
+        co = O.mvdr_weights(Rs[g], a)
+        assert rel(c[off["woff"][g]:off["woff"][g + 1]], co) <= SOLVE_TOL, (g, rel(c[off["woff"][g]:off["woff"][g + 1]], co))
+
+
 def test_run_host_matches_run():
     cfg = all_configs()["C1"]
     sc = make_scene(cfg)
