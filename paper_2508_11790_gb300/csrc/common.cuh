@@ -159,6 +159,36 @@ __device__ __forceinline__ void stockham_pass(int tid, const float2 *__restrict_
     }
 }
 
+// Double-float values (h + l, |l| <= ulp(h)/2): GB300's FP64 pipe is
+// narrow, so the covariance epilogues assemble R in FP32 pairs and convert
+// only the final value of each entry to FP64.
+struct DF {
+    float h, l;
+};
+__device__ __forceinline__ DF df_norm(float h, float l) {   // |l| small against h
+    const float s = h + l;
+    return DF{s, l - (s - h)};
+}
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+    const float s = a.h + b.h;
+    const float bb = s - a.h;
+    const float e = (a.h - (s - bb)) + (b.h - bb) + a.l + b.l;
+    return df_norm(s, e);
+}
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+    const float p = a.h * b.h;
+    float e = fmaf(a.h, b.h, -p);
+    e = fmaf(a.h, b.l, e);
+    e = fmaf(a.l, b.h, e);
+    return df_norm(p, e);
+}
+__device__ __forceinline__ double df_to_double(DF a) { return (double)a.h + (double)a.l; }
+// host side: a double as a double-float (for kernel parameters)
+inline DF df_from_double(double v) {
+    const float h = (float)v;
+    return DF{h, (float)(v - (double)h)};
+}
+
 // Padded shared-memory row index: one spare slot every 16 rows spreads the
 // radix-16 strided accesses over the banks.
 __device__ __forceinline__ int padrow(int t) { return t + (t >> 4); }

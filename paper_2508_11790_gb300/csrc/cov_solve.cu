@@ -21,6 +21,7 @@ bs_status launch_cov_solve(const bs_plan *p, const void *ztr, const float *delta
     a.pairs = p->pairs;
     a.delta_pair = delta;
     a.delta = p->cfg.delta;
+    a.delta_df = df_from_double(p->cfg.delta);
     a.inv_sc = 1.0f / p->cfg.store_scale;
     a.kappa_max = p->cfg.kappa_max;
     a.refine = (p->cfg.flags & BS_FLAG_NO_REFINE) ? 0 : 1;
@@ -64,6 +65,7 @@ bs_status launch_cov_solve_tables(const void *z, int precision, float store_scal
     a.pairs = pairs;
     a.delta_pair = nullptr;
     a.delta = delta;
+    a.delta_df = df_from_double(delta);
     a.inv_sc = 1.0f / store_scale;
     a.kappa_max = kappa_max;
     a.refine = (flags & BS_FLAG_NO_REFINE) ? 0 : 1;

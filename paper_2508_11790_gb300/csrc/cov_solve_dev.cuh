@@ -10,7 +10,8 @@
 //      (read-only path) and does 9 complex multiply-adds; FP32 sums cover
 //      at most 16 vectors and are folded into double-float (hi, lo);
 //   2. reduces the slices in double-float and forms R = sum / K + delta I in
-//      FP64 in its shared memory (optionally also stored);
+//      double-float, stored as FP64 in its shared memory (optionally also in
+//      global memory);
 //   3. solves (solve_pair: FP32 Cholesky, FP64-residual refinement, FP64
 //      escalation) and writes c and info.
 // No CTA-wide barrier is involved, so one half-warp's solve overlaps the
@@ -54,6 +55,7 @@ struct CovSolveArgs {
     int64_t pairs;
     const float *delta_pair;  // NULL: delta
     double delta;
+    DF delta_df;              // delta as a double-float
     float inv_sc;
     double kappa_max;
     int refine, allow_f64;
@@ -148,9 +150,12 @@ __global__ void __launch_bounds__(NTH) cov_solve_kernel(CovSolveArgs a) {
         }
         __syncwarp(mask);
 
-        // slice reduction (double-float) and the loaded FP64 covariance
-        const double invK = 1.0 / (double)K;
-        const double d = a.delta_pair ? (double)a.delta_pair[g] : a.delta;
+        // slice reduction and the loaded covariance in double-float; FP64 only
+        // for the stored value of each entry
+        const float Kf = (float)K;
+        const float qk = 1.f / Kf;
+        const DF invK = df_norm(qk, fmaf(-qk, Kf, 1.f) / Kf);   // 1/K (K < 2^24)
+        const DF dl = a.delta_pair ? DF{a.delta_pair[g], 0.f} : a.delta_df;
         const int E = W * (W + 1) / 2;
         for (int e = lane; e < E; e += 16) {
             int i = 0, r2 = e;
@@ -166,13 +171,13 @@ __global__ void __launch_bounds__(NTH) cov_solve_kernel(CovSolveArgs a) {
                 df_acc(th, tl, o[2]);
                 tl += o[3];
             }
-            const double re = ((double)sh + (double)sl) * invK;
-            const double im = ((double)th + (double)tl) * invK;
+            const DF re = df_mul(df_norm(sh, sl), invK);
             if (i == j) {
-                S.R[i * W + i] = make_double2(re + d, 0.0);
+                S.R[i * W + i] = make_double2(df_to_double(df_add(re, dl)), 0.0);
             } else {
-                S.R[i * W + j] = make_double2(re, im);
-                S.R[j * W + i] = make_double2(re, -im);
+                const double rd = df_to_double(re), id = df_to_double(df_mul(df_norm(th, tl), invK));
+                S.R[i * W + j] = make_double2(rd, id);
+                S.R[j * W + i] = make_double2(rd, __longlong_as_double(__double_as_longlong(id) ^ (1ll << 63)));
             }
         }
         __syncwarp(mask);

@@ -74,30 +74,6 @@ __device__ __forceinline__ void df_fold(float &hi, float &lo, float b) {
     hi = s;
 }
 
-// Double-float values (h + l, |l| <= ulp(h)/2) for the epilogue: GB300's
-// FP64 pipe is narrow, so R is assembled in FP32 pairs and only the final
-// value of each entry is converted to FP64.
-struct DF {
-    float h, l;
-};
-__device__ __forceinline__ DF df_norm(float h, float l) {   // |l| small against h
-    const float s = h + l;
-    return DF{s, l - (s - h)};
-}
-__device__ __forceinline__ DF df_add(DF a, DF b) {
-    const float s = a.h + b.h;
-    const float bb = s - a.h;
-    const float e = (a.h - (s - bb)) + (b.h - bb) + a.l + b.l;
-    return df_norm(s, e);
-}
-__device__ __forceinline__ DF df_mul(DF a, DF b) {
-    const float p = a.h * b.h;
-    float e = fmaf(a.h, b.h, -p);
-    e = fmaf(a.h, b.l, e);
-    e = fmaf(a.l, b.h, e);
-    return df_norm(p, e);
-}
-__device__ __forceinline__ double df_to_double(DF a) { return (double)a.h + (double)a.l; }
 
 template <int PREC>
 __global__ void __launch_bounds__(MMA_WARPS * 32)
@@ -254,11 +230,6 @@ __global__ void __launch_bounds__(MMA_WARPS * 32)
     }
 }
 
-static DF split_df(double v) {
-    const float h = (float)v;
-    return DF{h, (float)(v - (double)h)};
-}
-
 bs_status launch_window_cov_mma(const bs_plan *p, const void *ztr, const float *delta, double2 *R,
                                 cudaStream_t st) {
     const int64_t G = p->pairs;
@@ -273,8 +244,8 @@ bs_status launch_window_cov_mma(const bs_plan *p, const void *ztr, const float *
         if (e != cudaSuccess) return cuda_error(e, "covariance (tensor core) attribute");
         attr_set = true;
     }
-    const DF sc = split_df(1.0 / ((double)p->cfg.store_scale * (double)p->cfg.store_scale));
-    const DF dl = split_df(p->cfg.delta);
+    const DF sc = df_from_double(1.0 / ((double)p->cfg.store_scale * (double)p->cfg.store_scale));
+    const DF dl = df_from_double(p->cfg.delta);
     if (p->cfg.precision == BS_PREC_FP16)
         window_cov_mma_kernel<BS_PREC_FP16><<<blocks, MMA_WARPS * 32, MMA_SMEM, st>>>(
             ztr, p->d_ztr_off, p->d_Wg, p->d_Kg, p->d_roff, delta, dl, sc, R, G);
