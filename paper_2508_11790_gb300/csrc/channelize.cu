@@ -79,7 +79,10 @@ __global__ void __launch_bounds__(ChCfg<F>::nthr, ChCfg<F>::minb)
 // tiles.  The raw tile (F rows x NT columns) arrives in a dense staging
 // buffer by TMA; pass 0 reads it into the padded work buffer, after which
 // the staging buffer is free and the next tile's TMA is issued, so the HBM
-// reads of tile i+1 overlap passes 1-2 (and the HBM writes) of tile i.
+// reads of tile i+1 overlap passes 1-2 (and the HBM writes) of tile i.  The
+// last pass writes a dense output tile in shared memory, which leaves by
+// TMA tensor stores (NT x 8-byte rows, clipped at N): scattered 8-byte
+// stores from every thread had filled the global store queue.
 template <int F>
 struct ChTmaCfg {
     static constexpr int NT = ChCfg<F>::NT;
@@ -87,13 +90,13 @@ struct ChTmaCfg {
     static constexpr int box_rows = F < 256 ? F : 256;
     static constexpr size_t stage_bytes = (size_t)F * NT * sizeof(float2);
     static constexpr size_t work_bytes = (size_t)padded_len(F) * NT * sizeof(float2);
-    static constexpr size_t smem = stage_bytes + work_bytes + 16;
+    static constexpr size_t smem = 2 * stage_bytes + work_bytes + 16;   // staging, work, output tile
 };
 
 template <int F>
 __global__ void __launch_bounds__(ChTmaCfg<F>::nthr, 1)
-    channelize_tma_kernel(const __grid_constant__ CUtensorMap tmap, float2 *__restrict__ xc, int N, int P,
-                          const float2 *__restrict__ tw, float scale, int *__restrict__ err) {
+    channelize_tma_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap omap, int N,
+                          int P, const float2 *__restrict__ tw, float scale, int *__restrict__ err) {
     using RP = Radix<F>;
     using C = ChTmaCfg<F>;
     constexpr int NT = C::NT;
@@ -101,7 +104,8 @@ __global__ void __launch_bounds__(ChTmaCfg<F>::nthr, 1)
     extern __shared__ __align__(128) unsigned char smraw[];
     float2 *stg = reinterpret_cast<float2 *>(smraw);
     float2 *sm = reinterpret_cast<float2 *>(smraw + C::stage_bytes);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smraw + C::stage_bytes + C::work_bytes);
+    float2 *ob = reinterpret_cast<float2 *>(smraw + C::stage_bytes + C::work_bytes);   // dense output tile
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smraw + 2 * C::stage_bytes + C::work_bytes);
     __shared__ int ok_s;
     const int tid = threadIdx.x;
     const int ntn = (N + NT - 1) / NT;
@@ -132,38 +136,39 @@ __global__ void __launch_bounds__(ChTmaCfg<F>::nthr, 1)
             if (tid == 0) {
                 atomicOr(err, 1);
                 mbar_wait_bounded(bar, phase);
+                bulk_wait0();
             }
             return;
         }
         mbar_try_wait(bar, phase);   // completed phase: each thread acquires the TMA writes
         phase ^= 1u;
-        float2 *xout = xc + (size_t)p * F * N;
         auto gload = [&](int c, int t) -> float2 {
             const float2 v = stg[t * NT + c];
             return (t & 1) ? make_float2(-v.x, -v.y) : v;   // (-1)^t: signed-frequency order
         };
         auto sload = [&](int c, int t) -> float2 { return sm[padrow(t) * NT + c]; };
         auto sstore = [&](int c, int t, float2 v) { sm[padrow(t) * NT + c] = v; };
-        auto gstore = [&](int c, int q, float2 v) {
-            const int n = n0 + c;
-            if (n < N) xout[(size_t)q * N + n] = cscale(v, scale);
-        };
-        static_assert(RP::npass == 3 || RP::npass == 2, "TMA channeliser needs F >= 32");
+        auto ostore = [&](int c, int q, float2 v) { ob[q * NT + c] = cscale(v, scale); };
+        static_assert(RP::npass == 3, "TMA channeliser needs F >= 512");
         stockham_pass<F, RP::r0, 1, NT, nthr, true, false>(tid, tw, gload, sstore);
         __syncthreads();   // staging consumed
         if (tid == 0 && tile + gridDim.x < ntiles) {
             fence_proxy_async();
             issue(tile + gridDim.x);
         }
-        if constexpr (RP::npass == 3) {
-            stockham_pass<F, RP::r1, RP::r0, NT, nthr, true, true>(tid, tw, sload, sstore);
-            __syncthreads();
-            stockham_pass<F, RP::r2, RP::r0 * RP::r1, NT, nthr, true, false>(tid, tw, sload, gstore);
-        } else {
-            stockham_pass<F, RP::r1, RP::r0, NT, nthr, true, false>(tid, tw, sload, gstore);
+        stockham_pass<F, RP::r1, RP::r0, NT, nthr, true, true>(tid, tw, sload, sstore);
+        if (tid == 0) bulk_wait_read0();   // the previous tile's output has left the output buffer
+        __syncthreads();
+        stockham_pass<F, RP::r2, RP::r0 * RP::r1, NT, nthr, true, false>(tid, tw, sload, ostore);
+        __syncthreads();   // output tile complete; work buffer consumed before the next tile's pass 0
+        if (tid == 0) {    // output tile to xc by TMA (columns beyond N are clipped)
+            fence_proxy_async();
+#pragma unroll 1
+            for (int r0 = 0; r0 < F; r0 += C::box_rows) tma_store_2d(&omap, ob + (size_t)r0 * NT, 2 * n0, p * F + r0);
+            bulk_commit();
         }
-        __syncthreads();   // work buffer consumed before the next tile's pass 0
     }
+    if (tid == 0) bulk_wait0();
 }
 
 static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
@@ -187,13 +192,17 @@ static bs_status launch_ch_tma(const bs_plan *pl, const float2 *x, int P, int N,
     if ((N & 1) || (reinterpret_cast<uintptr_t>(x) & 15) || C::smem > 220 * 1024) return BS_OK;
     PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     if (!enc) return BS_OK;
-    CUtensorMap tmap;
+    if (reinterpret_cast<uintptr_t>(xc) & 15) return BS_OK;
+    CUtensorMap tmap, omap;
     const cuuint64_t gdim[2] = {(cuuint64_t)2 * N, (cuuint64_t)P * F};
     const cuuint64_t gstride[1] = {(cuuint64_t)N * sizeof(float2)};
     const cuuint32_t box[2] = {(cuuint32_t)(2 * C::NT), (cuuint32_t)C::box_rows};
     const cuuint32_t estr[2] = {1, 1};
     if (enc(&tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float2 *>(x), gdim, gstride, box, estr,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS ||
+        enc(&omap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, xc, gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return BS_OK;   // fall back to the non-TMA kernel
     static bool attr_set = false;
@@ -205,7 +214,7 @@ static bs_status launch_ch_tma(const bs_plan *pl, const float2 *x, int P, int N,
     }
     const long long tiles = (long long)P * ((N + C::NT - 1) / C::NT);
     const int grid = (int)std::min<long long>(tiles, pl->num_sms);
-    channelize_tma_kernel<F><<<grid, C::nthr, C::smem, st>>>(tmap, xc, N, P, pl->d_twF, 1.0f / sqrtf((float)F),
+    channelize_tma_kernel<F><<<grid, C::nthr, C::smem, st>>>(tmap, omap, N, P, pl->d_twF, 1.0f / sqrtf((float)F),
                                                             pl->d_err);
     *used = true;
     return check_launch("channelize (TMA) launch");
