@@ -180,6 +180,7 @@ bs_status launch_beamspace(const bs_plan *p, const float2 *xc, void *ztr, float2
     ga.P_train = p->cfg.P_train;
     ga.uniform = (p->B % p->vpb) == 0;
     ga.gather = p->d_gather;
+    ga.gsub = reinterpret_cast<const longlong2 *>(p->d_gsub);
     ga.ngather = (int)p->gather.size();
     ga.Wg = p->d_Wg;
     ga.Kg = p->d_Kg;

@@ -198,11 +198,19 @@ __global__ void __launch_bounds__(256, 2)
             fence_proxy_async();
             issue(g + 2 * G, s);
         }
-        // this group's gather entries: loads issued here, stored after pass 3
+        // this group's gather entries (subband-major table: one contiguous
+        // read for consecutive targets); loads issued here, stored after pass 3
         long long e_base = 0;
         int e_sw = 0, e_n = 0;
         const bool filler = tid < ga.T && tid < kTabT;
-        if (filler) fill_target_entry(ga, tid, sb, v0, vpb, train, &e_base, &e_sw, &e_n, 0);
+        if (filler) {
+            const longlong2 *gs = ga.gsub + 2 * ((int64_t)sb * ga.T + tid);
+            const longlong2 o = __ldg(gs), m = __ldg(gs + 1);
+            const int W = (int)(m.x >> 16), K = (int)m.y;
+            e_sw = (int)m.x;
+            e_n = train ? ((v0 >= K) ? 0 : min(vpb * W, (K - v0) * W)) : vpb * W;
+            e_base = (train ? o.x : o.y) + (long long)v0 * W;
+        }
 
         // pass 2: radix 16, Ns = 16, X1 -> X2
         {

@@ -117,6 +117,7 @@ void bs_plan_destroy(bs_plan *p) {
     cudaFree(p->d_Wg);
     cudaFree(p->d_Kg);
     cudaFree(p->d_gather);
+    cudaFree(p->d_gsub);
     cudaFree(p->d_woff);
     cudaFree(p->d_ztr_off);
     cudaFree(p->d_zte_off);
@@ -253,6 +254,18 @@ bs_status bs_plan_create(bs_plan **out, const bs_config *cfg) {
     for (int t = 0; t < c.T; ++t)
         for (int cc = 0; cc < p->vpb; ++cc)
             for (int w = 0; w < p->Wt[t]; ++w) p->gather.push_back((t << 8) | (cc << 4) | w);
+    // the same per-pair fields subband-major, so that the per-group entries
+    // of consecutive targets are one contiguous read
+    p->gsub.resize((size_t)4 * G);
+    for (int s = 0; s < c.L; ++s)
+        for (int t = 0; t < c.T; ++t) {
+            const int64_t g = (int64_t)t * c.L + s;
+            int64_t *e = &p->gsub[(size_t)4 * ((int64_t)s * c.T + t)];
+            e[0] = p->ztr_off[g];
+            e[1] = p->zte_off[g];
+            e[2] = (int64_t)(p->start[g] | (p->Wg[g] << 16));
+            e[3] = p->Kg[g];
+        }
 
     // work-queue order of the fused covariance + solve: decreasing W^2 K
     p->order.resize(G);
@@ -267,6 +280,7 @@ bs_status bs_plan_create(bs_plan **out, const bs_config *cfg) {
     if (!st) st = upload(&p->d_Wg, p->Wg);
     if (!st) st = upload(&p->d_Kg, p->Kg);
     if (!st) st = upload(&p->d_gather, p->gather);
+    if (!st) st = upload(&p->d_gsub, p->gsub);
     if (!st) st = upload(&p->d_woff, p->woff);
     if (!st) st = upload(&p->d_ztr_off, p->ztr_off);
     if (!st) st = upload(&p->d_zte_off, p->zte_off);
