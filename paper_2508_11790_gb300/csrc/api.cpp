@@ -1,5 +1,6 @@
 // extern "C" entry points of the hot path: argument checks, then the
 // kernel launchers of the individual translation units.
+#include <algorithm>
 #include <string>
 
 #include "internal.h"
@@ -197,13 +198,44 @@ bs_status bs_set_launch(bs_plan *p, int32_t threads, int32_t ctas_per_sm) {
 bs_status bs_run_host(const bs_plan *p, const bs_cf32 *x_host, bs_cf32 *out_host, const bs_buffers *b,
                       bs_stream stream) {
     BS_REQUIRE(p && b && x_host && out_host, "NULL argument");
-    BS_REQUIRE(b->x && b->out, "buf->x and buf->out must be device buffers");
+    BS_REQUIRE(b->x && b->xc && b->z_train && b->out, "buf->x, xc, z_train and out must be device buffers");
+    BS_REQUIRE(b->z_test || p->cfg.P_test == 0, "z_test is NULL but P_test > 0");
+    if (bs_status s = check_device(p)) return s;
     const cudaStream_t st = (cudaStream_t)stream;
-    const size_t xbytes = (size_t)p->P * p->cfg.F * p->cfg.N * sizeof(bs_cf32);
+    const size_t rec = (size_t)p->cfg.F * p->cfg.N;   // elements per record
     const size_t obytes = (size_t)p->pairs * p->Vte * sizeof(bs_cf32);
-    cudaError_t e = cudaMemcpyAsync((void *)b->x, x_host, xbytes, cudaMemcpyHostToDevice, st);
+    // Record chunks: the copy of chunk k+1 (on the plan's copy stream) runs
+    // while chunk k is channelised and transformed on `stream`; the host link
+    // is slower than the two stages, so only the last chunk's work and the
+    // covariance, solve and apply remain after the last copy.
+    const int P = p->P;
+    const int per = (P + bs_plan::kHostChunks - 1) / bs_plan::kHostChunks;
+    cudaError_t e = cudaEventRecord(p->ev_start, st);   // earlier work on `stream` is done with x
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(p->copy_st, p->ev_start, 0);
+    for (int k = 0, p0 = 0; p0 < P && e == cudaSuccess; ++k, p0 += per) {
+        const int np = std::min(per, P - p0);
+        e = cudaMemcpyAsync((void *)(b->x + p0 * rec), x_host + p0 * rec, np * rec * sizeof(bs_cf32),
+                            cudaMemcpyHostToDevice, p->copy_st);
+        if (e == cudaSuccess) e = cudaEventRecord(p->ev_chunk[k], p->copy_st);
+    }
     if (e != cudaSuccess) return bs::cuda_error(e, "host to device copy");
-    if (bs_status s = bs_run(p, b, stream)) return s;
+    for (int k = 0, p0 = 0; p0 < P; ++k, p0 += per) {
+        const int np = std::min(per, P - p0);
+        e = cudaStreamWaitEvent(st, p->ev_chunk[k], 0);
+        if (e != cudaSuccess) return bs::cuda_error(e, "stream wait");
+        if (bs_status s = bs::launch_channelize(p, (const float2 *)(b->x + p0 * rec), np, (float2 *)(b->xc + p0 * rec), st))
+            return s;
+        if (bs_status s = bs::launch_beamspace(p, (const float2 *)b->xc, b->z_train, (float2 *)b->z_test, st, p0, np))
+            return s;
+    }
+    bs_status s;
+    if (p->cfg.flags & BS_FLAG_FUSED) {
+        if ((s = bs_cov_solve(p, b->z_train, nullptr, b->R, b->c, b->info, stream))) return s;
+    } else {
+        if ((s = bs_window_cov(p, b->z_train, nullptr, b->R, stream))) return s;
+        if ((s = bs_mvdr_solve(p, b->R, b->c, b->info, stream))) return s;
+    }
+    if ((s = bs_apply(p, b->z_test, b->c, b->out, stream))) return s;
     if (obytes) {
         e = cudaMemcpyAsync(out_host, b->out, obytes, cudaMemcpyDeviceToHost, st);
         if (e != cudaSuccess) return bs::cuda_error(e, "device to host copy");

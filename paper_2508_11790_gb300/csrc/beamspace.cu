@@ -34,8 +34,8 @@ __global__ void __launch_bounds__(BsCfg<M>::nthr, BsCfg<M>::minb)
     bool train_cta = false;
     if constexpr (!kFull) {
         if (ga.uniform && vid0 < ga.nvec) {
-            const int p = (int)(vid0 >> ga.log2F);
-            const int q = (int)(vid0 & ((1 << ga.log2F) - 1));
+            const int p = (int)((ga.vbase + vid0) >> ga.log2F);
+            const int q = (int)((ga.vbase + vid0) & ((1 << ga.log2F) - 1));
             s_cta = q >> ga.log2B;
             const int i0 = q & ((1 << ga.log2B) - 1);
             train_cta = p < ga.P_train;
@@ -110,8 +110,8 @@ __global__ void __launch_bounds__(BsCfg<M>::nthr, BsCfg<M>::minb)
             const int W = __ldg(&ga.Wg[g0]);
             const int64_t vid = vid0 + c;
             if (vid >= nvec) continue;
-            const int p = (int)(vid >> ga.log2F);
-            const int q = (int)(vid & Fm1);
+            const int p = (int)((ga.vbase + vid) >> ga.log2F);
+            const int q = (int)((ga.vbase + vid) & Fm1);
             const int s = q >> ga.log2B, i = q & Bm1;
             const int64_t g = g0 + s;
             const int m = (__ldg(&ga.start[g]) + w) & (M - 1);
@@ -170,9 +170,13 @@ static int ilog2(int v) {
     return r;
 }
 
-bs_status launch_beamspace(const bs_plan *p, const float2 *xc, void *ztr, float2 *zte, cudaStream_t st) {
+bs_status launch_beamspace(const bs_plan *p, const float2 *xc, void *ztr, float2 *zte, cudaStream_t st, int p0,
+                           int np) {
+    if (np < 0) np = p->P - p0;
     GatherArgs ga;
-    ga.nvec = (int64_t)p->P * p->cfg.F;
+    ga.nvec = (int64_t)np * p->cfg.F;
+    ga.vbase = (int64_t)p0 * p->cfg.F;
+    xc += ga.vbase * p->cfg.N;   // the kernels index vectors of this range
     ga.log2F = ilog2(p->cfg.F);
     ga.log2B = ilog2(p->B);
     ga.L = p->cfg.L;

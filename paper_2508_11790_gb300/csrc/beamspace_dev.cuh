@@ -21,7 +21,8 @@ struct BsCfg {
 };
 
 struct GatherArgs {
-    int64_t nvec;           // vectors = P * F
+    int64_t nvec;           // vectors of this launch (a whole number of records)
+    int64_t vbase;          // index of its first vector in the cube (multiple of F)
     int log2F, log2B, L, P_train, T;
     int uniform;            // B % vpb == 0: the vectors of a CTA share (record, subband)
     const int32_t *gather;  // [vpb * sumW] (t << 8) | (c << 4) | w

@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(256, 2)
             return;
         }
         mbar_try_wait(&bar[s], (it >> 1) & 1u);   // completed phase: each thread acquires the copy
-        const int64_t vid0 = g * vpb;
+        const int64_t vid0 = ga.vbase + g * vpb;   // in the whole cube
         const int p = (int)(vid0 >> ga.log2F);
         const int q = (int)(vid0 & ((1 << ga.log2F) - 1));
         const int sb = q >> ga.log2B;

@@ -43,6 +43,10 @@ struct bs_plan {
     double2 *d_at64 = nullptr;
     float2 *d_twF = nullptr, *d_twM = nullptr;   // e^{-2 pi i k / F}, e^{-2 pi i k / M}
     int *d_err = nullptr;                        // device error word (bit 0: a bounded wait gave up)
+    // bs_run_host: copy stream and events of its record-chunk pipeline
+    static constexpr int kHostChunks = 8;
+    cudaStream_t copy_st = nullptr;
+    cudaEvent_t ev_start = nullptr, ev_chunk[kHostChunks] = {};
     int num_sms = 0;
     // fused covariance + solve: queue order (decreasing W^2 K), workspace head
     std::vector<int32_t> order;
@@ -59,7 +63,9 @@ bs_status check_launch(const char *where);
 
 // kernel launchers (one per translation unit)
 bs_status launch_channelize(const bs_plan *p, const float2 *x, int P, float2 *xc, cudaStream_t st);
-bs_status launch_beamspace(const bs_plan *p, const float2 *xc, void *ztr, float2 *zte, cudaStream_t st);
+// records p0 .. p0+np-1 (np < 0: through the last record)
+bs_status launch_beamspace(const bs_plan *p, const float2 *xc, void *ztr, float2 *zte, cudaStream_t st, int p0 = 0,
+                           int np = -1);
 bs_status launch_beamspace_full(const bs_plan *p, const float2 *y, int64_t nvec, float2 *yb,
                                 cudaStream_t st);
 bs_status launch_window_cov(const bs_plan *p, const void *ztr, const float *delta, double2 *R,

@@ -130,6 +130,10 @@ void bs_plan_destroy(bs_plan *p) {
     cudaFree(p->d_err);
     cudaFree(p->d_order);
     cudaFree(p->d_head);
+    for (cudaEvent_t e : p->ev_chunk)
+        if (e) cudaEventDestroy(e);
+    if (p->ev_start) cudaEventDestroy(p->ev_start);
+    if (p->copy_st) cudaStreamDestroy(p->copy_st);
     delete p;
 }
 
@@ -293,6 +297,10 @@ bs_status bs_plan_create(bs_plan **out, const bs_config *cfg) {
     if (!st) st = upload(&p->d_err, std::vector<int>(1, 0));
     if (!st) st = upload(&p->d_order, p->order);
     if (!st) st = upload(&p->d_head, std::vector<int>(1, 0));
+    if (!st) st = bs::cuda_error(cudaStreamCreateWithFlags(&p->copy_st, cudaStreamNonBlocking), "copy stream");
+    if (!st) st = bs::cuda_error(cudaEventCreateWithFlags(&p->ev_start, cudaEventDisableTiming), "event");
+    for (int k = 0; k < bs_plan::kHostChunks && !st; ++k)
+        st = bs::cuda_error(cudaEventCreateWithFlags(&p->ev_chunk[k], cudaEventDisableTiming), "event");
     if (!st) st = bs::cuda_error(cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device),
                                  "device attribute");
     if (st) {

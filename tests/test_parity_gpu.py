@@ -282,20 +282,32 @@ def test_solve_scale_invariance_and_split_edges():
         assert rel(c[off["woff"][g]:off["woff"][g + 1]], co) <= SOLVE_TOL, (g, rel(c[off["woff"][g]:off["woff"][g + 1]], co))
 
 
-def test_run_host_matches_run():
-    cfg = all_configs()["C1"]
+@pytest.mark.parametrize("name,precision,records", [("C1", P.BS_PREC_FP32, None), ("C2", P.BS_PREC_FP16, None),
+                                                    ("C2", P.BS_PREC_FP32, (13, 6))])
+def test_run_host_matches_run(name, precision, records):
+    """bs_run_host pipelines the host copy with channelisation and beamspace
+    in record chunks (P = 19 records: chunks of 3 and a ragged last one);
+    every intermediate and the output equal bs_run's bit for bit."""
+    cfg = all_configs()[name]
+    if records:
+        cfg = scaled_config(cfg, P_tr=records[0], P_te=records[1], K=min(cfg.K[0], records[0] * cfg.B))
     sc = make_scene(cfg)
-    plan = P.Plan.from_scene_config(cfg, sc.u_tgt)
+    plan = P.Plan.from_scene_config(cfg, sc.u_tgt, precision=precision)
     b = P.alloc_buffers(plan)
     b.x.copy_(torch.from_numpy(sc.x.reshape(-1)))
     P.bs_run(plan, b)
     torch.cuda.synchronize()
-    out_dev = b.out.cpu().clone()
+    ref = {k: getattr(b, k).cpu().clone() for k in ("xc", "z_train", "z_test", "R", "c", "out")}
     xh = torch.from_numpy(sc.x.reshape(-1)).pin_memory()
     oh = torch.empty(plan.sizes.out_elems, dtype=torch.complex64).pin_memory()
-    b.out.zero_()
+    for k in ref:
+        getattr(b, k).zero_()
+    b.x.zero_()
     P.bs_run_host(plan, xh, oh, b)
-    assert torch.equal(oh, out_dev[: plan.sizes.out_elems])
+    assert plan.device_status() == 0
+    assert torch.equal(oh, ref["out"][: plan.sizes.out_elems])
+    for k in ref:
+        assert torch.equal(getattr(b, k).cpu(), ref[k]), k
 
 
 def test_no_test_records_and_single_subband_bins():
