@@ -11,6 +11,8 @@ Default workload: N=1024 elements, F=2048, L=128 subbands, M=2048, W=9,
 K=512, T=64 targets (8192 pairs), 32 training + 8 test records (671 MB raw
 cube, larger than L2, so no flush is needed between steps), FP16 training
 windows (the mixed-precision configuration); --precision fp32 for FP32.
+The other workloads (--workload C1, C2, C4, C5) default to FP32 windows,
+the precision their configurations name.
 
 Arms:  --impl ours (default): the CUDA path through the C ABI.
        --impl reference: the FP64 CPU oracle on the host cores, one bounded
@@ -48,7 +50,8 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="C3")
-    ap.add_argument("--precision", choices=["fp32", "fp16", "bf16"], default="fp16")
+    ap.add_argument("--precision", choices=["fp32", "fp16", "bf16"], default=None,
+                    help="window precision (default: fp16 for C3, fp32 otherwise)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
@@ -57,7 +60,10 @@ def parse_args():
     ap.add_argument("--fused", action="store_true", help="fused persistent covariance + solve kernel")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="budget of the oracle sample timed for cpu_baseline")
-    return ap.parse_args()
+    a = ap.parse_args()
+    if a.precision is None:
+        a.precision = "fp16" if a.workload == "C3" else "fp32"
+    return a
 
 
 def load_peaks():
@@ -229,16 +235,17 @@ def algorithmic_bytes(plan, cfg):
     }
 
 
-def kernel_traffic(stage):
-    """DRAM bytes per launch of a stage from the committed ncu summary, if the
-    kernel source has not changed since it was taken (else None)."""
+def kernel_traffic(stage, workload):
+    """DRAM bytes per launch of a stage from the committed ncu summary, if it
+    was taken on this workload and precision and the kernel source has not
+    changed since (else None)."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(path):
         return None
     with open(path) as fh:
         d = json.load(fh)
     ent = d.get(stage)
-    if not ent:
+    if not ent or ent.get("workload") != workload:
         return None
     src = os.path.join(ROOT, ent["source"])
     if not os.path.exists(src):
@@ -385,7 +392,7 @@ def run_ours(args):
     dom = max(breakdown, key=breakdown.get)
     achieved = abytes[dom] / (breakdown[dom] / 1e3) / 1e9
     roofline = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
-                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": kernel_traffic(dom),
+                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": kernel_traffic(dom, f"{args.workload}/{args.precision}"),
                 "peak_source": f"{peak_kind} HBM copy bandwidth",
                 "algorithmic_bytes": abytes[dom]}
     per_stage = {k: {"ms": v, "GB/s": abytes[k] / (v / 1e3) / 1e9,
