@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(COV_THREADS)
     window_cov_kernel(const void *__restrict__ z, const int64_t *__restrict__ ztr_off,
                       const int32_t *__restrict__ Wg, const int32_t *__restrict__ Kg,
                       const int64_t *__restrict__ roff, const float *__restrict__ delta_pair,
-                      double delta, float inv_sc, double2 *__restrict__ R) {
+                      DF delta, float inv_sc, double2 *__restrict__ R) {
     constexpr int ES = (PREC == BS_PREC_FP32) ? 8 : 4;          // bytes per stored element
     __shared__ __align__(16) unsigned char stage[2][COV_STAGE_ELEMS * ES];
     __shared__ float red[4][9][COV_THREADS];
@@ -147,8 +147,11 @@ __global__ void __launch_bounds__(COV_THREADS)
         }
     __syncthreads();
 
-    const double invK = 1.0 / (double)K;
-    const double d = delta_pair ? (double)delta_pair[g] : delta;
+    // 1/K, the loading and R in double-float; FP64 only for the stored values
+    const float Kf = (float)K;
+    const float qk = 1.f / Kf;
+    const DF invK = df_norm(qk, fmaf(-qk, Kf, 1.f) / Kf);
+    const DF dl = delta_pair ? DF{delta_pair[g], 0.f} : delta;
     double2 *Rg = R + roff[g];
     const int E = W * (W + 1) / 2;
     for (int e = tid; e < E; e += COV_THREADS) {
@@ -165,13 +168,13 @@ __global__ void __launch_bounds__(COV_THREADS)
             df_add(th, tl, red[2][ee][o]);
             tl += red[3][ee][o];
         }
-        const double re = ((double)sh + (double)sl) * invK;
-        const double im = ((double)th + (double)tl) * invK;
+        const DF re = df_mul(df_norm(sh, sl), invK);
         if (i == j) {
-            Rg[i * W + i] = make_double2(re + d, 0.0);
+            Rg[i * W + i] = make_double2(df_to_double(df_add(re, dl)), 0.0);
         } else {
-            Rg[i * W + j] = make_double2(re, im);
-            Rg[j * W + i] = make_double2(re, -im);
+            const double rd = df_to_double(re), id = df_to_double(df_mul(df_norm(th, tl), invK));
+            Rg[i * W + j] = make_double2(rd, id);
+            Rg[j * W + i] = make_double2(rd, __longlong_as_double(__double_as_longlong(id) ^ (1ll << 63)));
         }
     }
 }
@@ -216,15 +219,15 @@ bs_status launch_window_cov(const bs_plan *p, const void *ztr, const float *delt
     switch (p->cfg.precision) {
         case BS_PREC_FP32:
             window_cov_kernel<BS_PREC_FP32><<<G, COV_THREADS, 0, st>>>(
-                ztr, p->d_ztr_off, p->d_Wg, p->d_Kg, p->d_roff, delta, p->cfg.delta, 1.0f, R);
+                ztr, p->d_ztr_off, p->d_Wg, p->d_Kg, p->d_roff, delta, df_from_double(p->cfg.delta), 1.0f, R);
             break;
         case BS_PREC_FP16:
             window_cov_kernel<BS_PREC_FP16><<<G, COV_THREADS, 0, st>>>(
-                ztr, p->d_ztr_off, p->d_Wg, p->d_Kg, p->d_roff, delta, p->cfg.delta, inv_sc, R);
+                ztr, p->d_ztr_off, p->d_Wg, p->d_Kg, p->d_roff, delta, df_from_double(p->cfg.delta), inv_sc, R);
             break;
         default:
             window_cov_kernel<BS_PREC_BF16><<<G, COV_THREADS, 0, st>>>(
-                ztr, p->d_ztr_off, p->d_Wg, p->d_Kg, p->d_roff, delta, p->cfg.delta, inv_sc, R);
+                ztr, p->d_ztr_off, p->d_Wg, p->d_Kg, p->d_roff, delta, df_from_double(p->cfg.delta), inv_sc, R);
             break;
     }
     return check_launch("covariance launch");
