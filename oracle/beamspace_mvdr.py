@@ -45,6 +45,8 @@ __all__ = [
     "mvdr_weights",
     "beamformer_output",
     "lifted_correlator",
+    "lifted_output",
+    "beam_pattern_grid",
     "beam_pattern",
     "output_sinr",
     "sinr_loss_db",
@@ -210,6 +212,20 @@ def lifted_correlator(c_tilde: np.ndarray, N: int, M: int, beams) -> np.ndarray:
 def beam_pattern(c: np.ndarray, a: np.ndarray) -> float:
     """|<c, a>| / (||c|| ||a||) (Eq. Cosine Sim), <c, a> = c^H a."""
     return float(abs(np.vdot(c, a)) / (np.linalg.norm(c) * np.linalg.norm(a)))
+
+
+def lifted_output(c_hat: np.ndarray, y: np.ndarray) -> np.ndarray:
+    """Output of the lifted correlator applied in antenna space (Sec. III-C,
+    below Eq. AntennaEqCorr): c_hat^H y for each row y of the channelised
+    antenna-domain snapshots, without the spatial FFT and window."""
+    return np.asarray(y, np.complex128) @ np.conj(np.asarray(c_hat, np.complex128))
+
+
+def beam_pattern_grid(c_hat: np.ndarray, u, f: float, fd: float) -> np.ndarray:
+    """Eq. Cosine Sim of c_hat against the steering vector of every direction
+    sine in u at frequency f (squinted spatial frequency, Eq. SubOmegaX)."""
+    N = len(c_hat)
+    return np.array([beam_pattern(c_hat, steering_vector(squinted_omega(float(uk), f, fd), N)) for uk in u])
 
 
 def output_sinr(c: np.ndarray, a: np.ndarray, R_in: np.ndarray) -> float:

@@ -318,3 +318,43 @@ def test_scene_training_records_are_target_free():
     tr = sc.x[: cfg.P_tr]
     assert np.mean(np.abs(tr) ** 2) == pytest.approx(cfg.sigma2, rel=0.02)
     assert np.mean(np.abs(sc.x[cfg.P_tr:]) ** 2) > 5 * cfg.sigma2
+
+
+def test_lifted_output_equals_windowed_beamspace_output():
+    """c_hat^H y = c~^H (S D y) (Sec. III-C, below Eq. AntennaEqCorr): the
+    lifted correlator applied in antenna space gives the windowed beamspace
+    output; the beamspace side is a brute-force DFT sum."""
+    N, M, W, start = 12, 32, 5, 29   # window wraps past beam M-1
+    ct = crandn(W)
+    y = crandn(7, N)
+    beams = O.window_beams(start, W, M)
+    ch = O.lifted_correlator(ct, N, M, beams)
+    n = np.arange(N)
+    zb = np.array([[np.sum(yy * np.exp(-2j * np.pi * m * n / M)) / np.sqrt(M) for m in beams] for yy in y])
+    np.testing.assert_allclose(O.lifted_output(ch, y), zb @ np.conj(ct), rtol=1e-12, atol=1e-12)
+
+
+def test_beam_pattern_grid_closed_forms():
+    """Eq. Cosine Sim: a matched filter c = a(Omega0) has the Dirichlet
+    pattern |sin(N d/2) / (N sin(d/2))|, d = Omega - Omega0; a distortionless
+    lifted MVDR correlator has pattern 1 / (||c_hat|| sqrt(N)) at its target."""
+    N, fd, f = 16, 10e9, 9.6e9
+    u = np.linspace(-0.95, 0.95, 41)
+    u0 = 0.3
+    om0 = O.squinted_omega(u0, f, fd)
+    pat = O.beam_pattern_grid(O.steering_vector(om0, N), u, f, fd)
+    d = np.array([O.squinted_omega(uk, f, fd) for uk in u]) - om0
+    with np.errstate(invalid="ignore", divide="ignore"):
+        dir_ = np.abs(np.sin(N * d / 2) / (N * np.sin(d / 2)))
+    dir_[np.abs(d) < 1e-12] = 1.0
+    np.testing.assert_allclose(pat, dir_, atol=1e-12)
+    # lifted MVDR weights of a window around u0
+    M, W = 32, 5
+    x = om0 * M / (2 * np.pi)
+    start = int(np.floor(x - W / 2 + 1)) % M
+    beams = O.window_beams(start, W, M)
+    at = O.windowed_steering(om0, N, M, beams)
+    R = _rand_pd(W, cond=50.0)
+    ch = O.lifted_correlator(O.mvdr_weights(R, at), N, M, beams)
+    p0 = O.beam_pattern_grid(ch, [u0], f, fd)[0]
+    assert p0 == pytest.approx(1.0 / (np.linalg.norm(ch) * np.sqrt(N)), rel=1e-12)
