@@ -266,6 +266,33 @@ bs_status bs_cov_solve_noalloc(const void *z_train, int32_t precision, float sto
 bs_status bs_apply(const bs_plan *plan, const bs_cf32 *z_test, const bs_cf32 *c,
                    bs_cf32 *out, bs_stream stream);
 
+/* Lifted correlator (Sec. III-C, Eq. AntennaEqCorr): c_hat_g = D^H S_g^T c_g,
+ * the antenna-space weights whose output c_hat_g^H y equals the windowed
+ * beamspace output c_g^H S_g D y.  c: weights packed as bs_mvdr_solve writes
+ * them ([pair][W_g], offsets woff); c_hat: [pair][N] cf32 (caller-owned
+ * device memory; pair g = t L + s).  Errors: BS_EINVAL for NULL buffers or a
+ * wrong device, BS_EUNSUPPORTED for W > 16. */
+bs_status bs_lift(const bs_plan *plan, const bs_cf32 *c, bs_cf32 *c_hat, bs_stream stream);
+
+/* The lifted correlator applied in antenna space (Sec. III-C, below Eq.
+ * AntennaEqCorr: no per-sample spatial FFT or window at inference):
+ * out[g][v'] = c_hat_g^H y_v', y_v' the channelised element vector xc[p][q]
+ * of test vector v' (record p = P_train + v'/B, bin q = s B + v' mod B) of
+ * pair g's subband s.  xc: [P][F][N] as bs_channelize writes it; c_hat as
+ * bs_lift writes it; out: [pair][Vte] cf32, the layout of bs_apply.  FP32
+ * arithmetic; equals bs_apply's output up to rounding. */
+bs_status bs_apply_lifted(const bs_plan *plan, const bs_cf32 *xc, const bs_cf32 *c_hat, bs_cf32 *out,
+                          bs_stream stream);
+
+/* Beam pattern of every lifted correlator (Eq. Cosine Sim):
+ * pattern[g][k] = |c_hat_g^H a(Omega_gk)| / (||c_hat_g|| sqrt(N)) with
+ * a(Omega) = [e^{j Omega n}]_n (Eq. ArrayX) and Omega_gk = pi u_k f_s / f_d,
+ * f_s the centre frequency of pair g's subband (Eq. SubOmegaX).  u: device
+ * array of n_dirs direction sines (FP64); pattern: device [pair][n_dirs]
+ * FP32.  Distortionless weights give 1 / (||c_hat|| sqrt(N)) at the target. */
+bs_status bs_beam_pattern(const bs_plan *plan, const bs_cf32 *c_hat, int32_t n_dirs, const double *u,
+                          float *pattern, bs_stream stream);
+
 /* The whole pass on device buffers: channelise, beamspace, covariance,
  * solve (bs_cov_solve with BS_FLAG_FUSED), apply (delta = plan delta). */
 bs_status bs_run(const bs_plan *plan, const bs_buffers *buf, bs_stream stream);

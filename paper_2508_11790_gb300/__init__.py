@@ -24,6 +24,7 @@ __all__ = [
     "BsError", "Plan", "Buffers", "alloc_buffers", "lib", "bs_plan_tables_host",
     "bs_channelize", "bs_beamspace", "bs_beamspace_full", "bs_window_cov",
     "bs_mvdr_solve", "bs_apply", "bs_run", "bs_run_host",
+    "bs_lift", "bs_apply_lifted", "bs_beam_pattern",
 ]
 
 BS_PREC_FP32, BS_PREC_FP16, BS_PREC_BF16 = 0, 1, 2
@@ -73,6 +74,9 @@ _SIGS = {
     "bs_window_cov": ([_P, _P, _P, _P, _P], ctypes.c_int),
     "bs_mvdr_solve": ([_P, _P, _P, _P, _P], ctypes.c_int),
     "bs_apply": ([_P, _P, _P, _P, _P], ctypes.c_int),
+    "bs_lift": ([_P, _P, _P, _P], ctypes.c_int),
+    "bs_apply_lifted": ([_P, _P, _P, _P, _P], ctypes.c_int),
+    "bs_beam_pattern": ([_P, _P, ctypes.c_int32, _P, _P, _P], ctypes.c_int),
     "bs_run": ([_P, ctypes.POINTER(_Buffers), _P], ctypes.c_int),
     "bs_run_host": ([_P, _P, _P, ctypes.POINTER(_Buffers), _P], ctypes.c_int),
     "bs_plan_tables_host": ([ctypes.POINTER(_Config), _P, _P], ctypes.c_int),
@@ -379,6 +383,32 @@ def bs_apply(plan: Plan, z_test: torch.Tensor, c: torch.Tensor, out: torch.Tenso
     _check(lib().bs_apply(plan.handle, _ptr(z_test, torch.complex64, s.ztest_elems, "z_test"),
                           _ptr(c, torch.complex64, s.c_elems, "c"),
                           _ptr(out, torch.complex64, s.out_elems, "out"), _stream(stream)), "bs_apply")
+
+
+def bs_lift(plan: Plan, c: torch.Tensor, c_hat: torch.Tensor, stream=None):
+    """Lifted correlators c_hat [pairs * N] (complex64) from the weights c."""
+    s = plan.sizes
+    _check(lib().bs_lift(plan.handle, _ptr(c, torch.complex64, s.c_elems, "c"),
+                         _ptr(c_hat, torch.complex64, s.pairs * plan.N, "c_hat"), _stream(stream)), "bs_lift")
+
+
+def bs_apply_lifted(plan: Plan, xc: torch.Tensor, c_hat: torch.Tensor, out: torch.Tensor, stream=None):
+    """out [pairs * Vte] = c_hat^H y on the channelised test vectors xc."""
+    s = plan.sizes
+    _check(lib().bs_apply_lifted(plan.handle, _ptr(xc, torch.complex64, s.xc_elems, "xc"),
+                                 _ptr(c_hat, torch.complex64, s.pairs * plan.N, "c_hat"),
+                                 _ptr(out, torch.complex64, s.out_elems, "out"), _stream(stream)),
+           "bs_apply_lifted")
+
+
+def bs_beam_pattern(plan: Plan, c_hat: torch.Tensor, u: torch.Tensor, pattern: torch.Tensor, stream=None):
+    """pattern [pairs * len(u)] (float32) of every lifted correlator at the
+    direction sines u (float64 device tensor)."""
+    s = plan.sizes
+    n = u.numel()
+    _check(lib().bs_beam_pattern(plan.handle, _ptr(c_hat, torch.complex64, s.pairs * plan.N, "c_hat"), n,
+                                 _ptr(u, torch.float64, n, "u"), _ptr(pattern, torch.float32, s.pairs * n, "pattern"),
+                                 _stream(stream)), "bs_beam_pattern")
 
 
 def _cbuf(plan: Plan, b: Buffers) -> _Buffers:

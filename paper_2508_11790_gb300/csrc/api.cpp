@@ -73,6 +73,33 @@ bs_status bs_apply(const bs_plan *p, const bs_cf32 *z_test, const bs_cf32 *c, bs
     return bs::launch_apply(p, (const float2 *)z_test, (const float2 *)c, (float2 *)out, (cudaStream_t)stream);
 }
 
+bs_status bs_lift(const bs_plan *p, const bs_cf32 *c, bs_cf32 *c_hat, bs_stream stream) {
+    BS_REQUIRE(p, "NULL plan");
+    BS_REQUIRE(c && c_hat, "NULL buffer");
+    if (bs_status s = check_device(p)) return s;
+    return bs::launch_lift(p, (const float2 *)c, (float2 *)c_hat, (cudaStream_t)stream);
+}
+
+bs_status bs_apply_lifted(const bs_plan *p, const bs_cf32 *xc, const bs_cf32 *c_hat, bs_cf32 *out,
+                          bs_stream stream) {
+    BS_REQUIRE(p, "NULL plan");
+    if (p->Vte == 0) return BS_OK;
+    BS_REQUIRE(xc && c_hat && out, "NULL buffer");
+    if (bs_status s = check_device(p)) return s;
+    return bs::launch_apply_lifted(p, (const float2 *)xc, (const float2 *)c_hat, (float2 *)out,
+                                   (cudaStream_t)stream);
+}
+
+bs_status bs_beam_pattern(const bs_plan *p, const bs_cf32 *c_hat, int32_t n_dirs, const double *u, float *pattern,
+                          bs_stream stream) {
+    BS_REQUIRE(p, "NULL plan");
+    BS_REQUIRE(n_dirs >= 0, "n_dirs must be >= 0");
+    if (n_dirs == 0) return BS_OK;
+    BS_REQUIRE(c_hat && u && pattern, "NULL buffer");
+    if (bs_status s = check_device(p)) return s;
+    return bs::launch_beam_pattern(p, (const float2 *)c_hat, n_dirs, u, pattern, (cudaStream_t)stream);
+}
+
 bs_status bs_cov_solve(const bs_plan *p, const void *z_train, const float *delta_pair, bs_cf64 *R, bs_cf32 *c,
                        int32_t *info, bs_stream stream) {
     BS_REQUIRE(p, "NULL plan");

@@ -85,5 +85,10 @@ bs_status launch_cov_solve_tables(const void *z, int precision, float store_scal
                                   uint32_t flags, float2 *c, int32_t *info, int *head, int grid,
                                   cudaStream_t st);
 int beamspace_vectors_per_cta(int M);
+bs_status launch_lift(const bs_plan *p, const float2 *c, float2 *c_hat, cudaStream_t st);
+bs_status launch_apply_lifted(const bs_plan *p, const float2 *xc, const float2 *c_hat, float2 *out,
+                              cudaStream_t st);
+bs_status launch_beam_pattern(const bs_plan *p, const float2 *c_hat, int n_dirs, const double *u, float *pattern,
+                              cudaStream_t st);
 
 }  // namespace bs

@@ -1,0 +1,189 @@
+// Lifted correlator (Sec. III-C, Eq. AntennaEqCorr), its antenna-space
+// application and its beam pattern (Eq. Cosine Sim).
+//
+// * lift: c_hat_g = D^H S_g^T c_g, i.e. c_hat_g[n] = M^-1/2 sum_w c_g[w]
+//   e^{+j 2 pi m_w n / M} with m_w = start_g + w (mod M); the exponentials
+//   are conjugated entries of the plan's M-point twiddle table (index
+//   m_w n mod M), so no transcendental is evaluated.  Thread per (pair, n).
+// * apply_lifted: out[g][v'] = c_hat_g^H y_v', y_v' the channelised
+//   antenna-domain vector of test vector v' of pair g's subband.  For one
+//   subband this is the complex product C^H Y of the [T][N] lifted weights
+//   and the [Vte][N] test vectors; a CTA computes a 32 x 32 tile of it with
+//   32-element slices of both staged in shared memory.  FP32 SIMT: the path
+//   keeps the accuracy of the FP32 test windows it stands in for.
+// * beam_pattern: |c_hat_g^H a(Omega)| / (||c_hat_g|| sqrt(N)) for a grid of
+//   direction sines u_k at pair g's squinted frequency, Omega = pi u_k f/f_d.
+//   A CTA per pair holds c_hat_g in shared memory; a warp per direction sums
+//   conj(c_hat[n]) e^{j Omega n} over its lanes' elements with a complex
+//   rotation per 32 elements (one sincospi per lane and per direction).
+#include "common.cuh"
+#include "internal.h"
+
+namespace bs {
+
+__global__ void __launch_bounds__(256)
+    lift_kernel(const float2 *__restrict__ c, const int64_t *__restrict__ woff, const int32_t *__restrict__ Wg,
+                const int32_t *__restrict__ start, const float2 *__restrict__ twM, int M, int N, float scale,
+                float2 *__restrict__ c_hat) {
+    const int64_t g = blockIdx.x;
+    const int n = blockIdx.y * blockDim.x + threadIdx.x;
+    __shared__ float2 cw[16];
+    __shared__ int mw[16];
+    const int W = Wg[g];
+    if (threadIdx.x < W) {
+        cw[threadIdx.x] = c[woff[g] + threadIdx.x];
+        mw[threadIdx.x] = (start[g] + threadIdx.x) & (M - 1);
+    }
+    __syncthreads();
+    if (n >= N) return;
+    float re = 0.f, im = 0.f;
+    for (int w = 0; w < W; ++w) {
+        const float2 t = __ldg(&twM[(mw[w] * n) & (M - 1)]);   // e^{-j 2 pi m n / M}
+        const float2 a = cw[w];
+        // a * conj(t)
+        re = fmaf(a.x, t.x, fmaf(a.y, t.y, re));
+        im = fmaf(a.y, t.x, fmaf(-a.x, t.y, im));
+    }
+    c_hat[g * N + n] = make_float2(re * scale, im * scale);
+}
+
+constexpr int AL_T = 32;   // targets per tile
+constexpr int AL_V = 32;   // test vectors per tile
+constexpr int AL_K = 32;   // elements per shared-memory slice
+
+// grid (ceil(T/32), ceil(Vte/32), L); 256 threads as 16 x 16, 2 x 2 outputs each
+__global__ void __launch_bounds__(256)
+    apply_lifted_kernel(const float2 *__restrict__ xc, const float2 *__restrict__ c_hat, float2 *__restrict__ out,
+                        int N, int F, int B, int L, int T, int P_train, int Vte) {
+    __shared__ float2 Cs[AL_T][AL_K + 1];
+    __shared__ float2 Ys[AL_V][AL_K + 1];
+    const int s = blockIdx.z;
+    const int t0 = blockIdx.x * AL_T, v0 = blockIdx.y * AL_V;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    float2 acc[2][2];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) acc[a][b] = make_float2(0.f, 0.f);
+    for (int k0 = 0; k0 < N; k0 += AL_K) {
+        // stage: row r of each tile, lanes along the elements (coalesced)
+        for (int e = threadIdx.x; e < AL_T * AL_K; e += 256) {
+            const int r = e / AL_K, k = e % AL_K;
+            const int t = t0 + r, v = v0 + r, n = k0 + k;
+            float2 cv = make_float2(0.f, 0.f), yv = make_float2(0.f, 0.f);
+            if (t < T && n < N) cv = __ldg(&c_hat[((int64_t)t * L + s) * N + n]);
+            if (v < Vte && n < N) {
+                const int p = P_train + v / B, q = s * B + v % B;
+                yv = __ldcs(&xc[((int64_t)p * F + q) * N + n]);
+            }
+            Cs[r][k] = cv;
+            Ys[r][k] = yv;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int k = 0; k < AL_K; ++k) {
+            const float2 c0 = Cs[2 * ty][k], c1 = Cs[2 * ty + 1][k];
+            const float2 y0 = Ys[2 * tx][k], y1 = Ys[2 * tx + 1][k];
+            const float2 cc[2] = {c0, c1}, yy[2] = {y0, y1};
+#pragma unroll
+            for (int a = 0; a < 2; ++a)
+#pragma unroll
+                for (int b = 0; b < 2; ++b) {   // conj(c) * y
+                    acc[a][b].x = fmaf(cc[a].x, yy[b].x, fmaf(cc[a].y, yy[b].y, acc[a][b].x));
+                    acc[a][b].y = fmaf(cc[a].x, yy[b].y, fmaf(-cc[a].y, yy[b].x, acc[a][b].y));
+                }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            const int t = t0 + 2 * ty + a, v = v0 + 2 * tx + b;
+            if (t < T && v < Vte) out[((int64_t)t * L + s) * Vte + v] = acc[a][b];
+        }
+}
+
+// one CTA per pair, a warp per direction
+__global__ void __launch_bounds__(256)
+    beam_pattern_kernel(const float2 *__restrict__ c_hat, const double *__restrict__ u, int n_dirs, int N, int L,
+                        double fc, double fs, double fd, float *__restrict__ pattern) {
+    extern __shared__ float2 ch[];
+    __shared__ float part[8];
+    const int64_t g = blockIdx.x;
+    const int s = (int)(g % L);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float nrm = 0.f;
+    for (int n = threadIdx.x; n < N; n += 256) {
+        const float2 v = c_hat[g * N + n];
+        ch[n] = v;
+        nrm = fmaf(v.x, v.x, fmaf(v.y, v.y, nrm));
+    }
+    for (int o = 16; o; o >>= 1) nrm += __shfl_xor_sync(0xFFFFFFFFu, nrm, o);
+    if (lane == 0) part[warp] = nrm;
+    __syncthreads();
+    float tot = 0.f;
+    for (int w = 0; w < 8; ++w) tot += part[w];
+    const float inv = 1.f / (sqrtf(tot) * sqrtf((float)N));
+    // subband centre frequency (Eq. SubChannelFreq): fc + ((l - 1/2) / L) fs,
+    // l = s - L/2 + 1, in this order
+    const double f = fc + (((double)(s - L / 2 + 1) - 0.5) / (double)L) * fs;
+    for (int k = warp; k < n_dirs; k += 8) {
+        // Omega / pi = u f / fd; e^{j Omega n} with n = lane + 32 i.  The two
+        // phases (in units of pi) are reduced to [-1, 1] in FP64 before the
+        // FP32 sincospi, so their error does not grow with n.
+        const double om = u[k] * (f / fd);
+        double x0 = om * (double)lane, x32 = om * 32.0;
+        x0 -= 2.0 * rint(0.5 * x0);
+        x32 -= 2.0 * rint(0.5 * x32);
+        float s0, c0, s32, c32;
+        sincospif((float)x0, &s0, &c0);
+        sincospif((float)x32, &s32, &c32);
+        float er = c0, ei = s0, re = 0.f, im = 0.f;
+        for (int n = lane; n < N; n += 32) {
+            const float2 a = ch[n];
+            // conj(a) * e
+            re = fmaf(a.x, er, fmaf(a.y, ei, re));
+            im = fmaf(a.x, ei, fmaf(-a.y, er, im));
+            const float nr = er * c32 - ei * s32;
+            ei = fmaf(er, s32, ei * c32);
+            er = nr;
+        }
+        for (int o = 16; o; o >>= 1) {
+            re += __shfl_xor_sync(0xFFFFFFFFu, re, o);
+            im += __shfl_xor_sync(0xFFFFFFFFu, im, o);
+        }
+        if (lane == 0) pattern[g * n_dirs + k] = sqrtf(re * re + im * im) * inv;
+    }
+}
+
+bs_status launch_lift(const bs_plan *p, const float2 *c, float2 *c_hat, cudaStream_t st) {
+    const int N = p->cfg.N;
+    if (p->pairs == 0) return BS_OK;
+    if (p->Wmax > 16) return set_error(BS_EUNSUPPORTED, "W > 16");
+    dim3 grid((unsigned)p->pairs, (N + 255) / 256);
+    lift_kernel<<<grid, 256, 0, st>>>(c, p->d_woff, p->d_Wg, p->d_start, p->d_twM, p->cfg.M, N,
+                                      1.0f / sqrtf((float)p->cfg.M), c_hat);
+    return check_launch("lift launch");
+}
+
+bs_status launch_apply_lifted(const bs_plan *p, const float2 *xc, const float2 *c_hat, float2 *out,
+                              cudaStream_t st) {
+    const int T = p->cfg.T, L = p->cfg.L, Vte = p->Vte;
+    if (Vte == 0 || p->pairs == 0) return BS_OK;
+    if (L > 65535) return set_error(BS_EUNSUPPORTED, "apply_lifted: at most 65535 subbands");
+    dim3 grid((T + AL_T - 1) / AL_T, (Vte + AL_V - 1) / AL_V, L);
+    apply_lifted_kernel<<<grid, 256, 0, st>>>(xc, c_hat, out, p->cfg.N, p->cfg.F, p->B, L, T, p->cfg.P_train, Vte);
+    return check_launch("apply_lifted launch");
+}
+
+bs_status launch_beam_pattern(const bs_plan *p, const float2 *c_hat, int n_dirs, const double *u, float *pattern,
+                              cudaStream_t st) {
+    if (n_dirs == 0 || p->pairs == 0) return BS_OK;
+    const size_t smem = (size_t)p->cfg.N * sizeof(float2);   // N <= 4096: <= 32 KB
+    beam_pattern_kernel<<<(unsigned)p->pairs, 256, smem, st>>>(c_hat, u, n_dirs, p->cfg.N, p->cfg.L, p->cfg.fc,
+                                                              p->cfg.fs, p->cfg.fd, pattern);
+    return check_launch("beam pattern launch");
+}
+
+}  // namespace bs
