@@ -384,6 +384,30 @@ def run_ours(args):
         ("mvdr_solve", lambda: P.bs_mvdr_solve(plan, b.R, b.c, b.info, stream=stream)),
     ], max(3, args.steps // 4))
     step()   # leave the timed path's results in the buffers
+    # lifted correlator (a row beyond the hot path): timed on its own, after
+    # the pass, on the pass's weights and channelised cube
+    lifted = None
+    if rank == 0:
+        c_hat = torch.empty(cfg.pairs * cfg.N, dtype=torch.complex64, device=dev)
+        out_l = torch.empty(max(plan.sizes.out_elems, 1), dtype=torch.complex64, device=dev)
+        n_dirs = 181
+        u_dirs = torch.linspace(-1.0, 1.0, n_dirs, dtype=torch.float64, device=dev)
+        pattern = torch.empty(cfg.pairs * n_dirs, dtype=torch.float32, device=dev)
+        lb = stage_breakdown([
+            ("lift", lambda: P.bs_lift(plan, b.c, c_hat, stream=stream)),
+            ("apply_lifted", lambda: P.bs_apply_lifted(plan, b.xc, c_hat, out_l, stream=stream)),
+            ("beam_pattern", lambda: P.bs_beam_pattern(plan, c_hat, u_dirs, pattern, stream=stream)),
+        ], max(3, args.steps // 4))
+        vte = plan.sizes.Vte
+        lift_bytes = cfg.pairs * cfg.N * 8 + plan.sizes.c_elems * 8
+        al_flops = 8.0 * cfg.pairs * vte * cfg.N
+        bp_flops = 8.0 * cfg.pairs * n_dirs * cfg.N
+        lifted = {"lift_ms": lb["lift"], "lift_GB/s": lift_bytes / (lb["lift"] / 1e3) / 1e9,
+                  "apply_lifted_ms": lb["apply_lifted"],
+                  "apply_lifted_TFLOP/s_fp32": al_flops / (lb["apply_lifted"] / 1e3) / 1e12,
+                  "beam_pattern_ms": lb["beam_pattern"], "beam_pattern_directions": n_dirs,
+                  "beam_pattern_TFLOP/s_fp32": bp_flops / (lb["beam_pattern"] / 1e3) / 1e12}
+        del c_hat, out_l, pattern
     clocks = sampler.stop()
     clocks["window"] = "plain-path, e2e, 1 s load soak, timed and per-stage loops (100 ms samples)"
     info = b.info.cpu().numpy()
@@ -441,7 +465,7 @@ def run_ours(args):
             "autotune": tune,
             "clocks": clocks, "stages": per_stage, "solve_core_ms": solve_core_ms,
             "other_solve_core_ms": other,
-            "plain_fp32": plain, "accuracy": accuracy,
+            "plain_fp32": plain, "accuracy": accuracy, "lifted_correlator": lifted,
             "info_counts": {str(k): int(v) for k, v in zip(*np.unique(info, return_counts=True))},
         }
         print(json.dumps(line), flush=True)

@@ -2,9 +2,11 @@
 // application and its beam pattern (Eq. Cosine Sim).
 //
 // * lift: c_hat_g = D^H S_g^T c_g, i.e. c_hat_g[n] = M^-1/2 sum_w c_g[w]
-//   e^{+j 2 pi m_w n / M} with m_w = start_g + w (mod M); the exponentials
-//   are conjugated entries of the plan's M-point twiddle table (index
-//   m_w n mod M), so no transcendental is evaluated.  Thread per (pair, n).
+//   e^{+j 2 pi m_w n / M} with m_w = start_g + w.  With z = e^{+j 2 pi n/M}
+//   this is M^-1/2 z^start (sum_w c_g[w] z^w), the sum by Horner's rule:
+//   two conjugated entries of the plan's M-point twiddle table per output
+//   (indices n and start n mod M) and no transcendental.  Thread per
+//   (pair, n).
 // * apply_lifted: out[g][v'] = c_hat_g^H y_v', y_v' the channelised
 //   antenna-domain vector of test vector v' of pair g's subband.  For one
 //   subband this is the complex product C^H Y of the [T][N] lifted weights
@@ -28,23 +30,17 @@ __global__ void __launch_bounds__(256)
     const int64_t g = blockIdx.x;
     const int n = blockIdx.y * blockDim.x + threadIdx.x;
     __shared__ float2 cw[16];
-    __shared__ int mw[16];
     const int W = Wg[g];
-    if (threadIdx.x < W) {
-        cw[threadIdx.x] = c[woff[g] + threadIdx.x];
-        mw[threadIdx.x] = (start[g] + threadIdx.x) & (M - 1);
-    }
+    if (threadIdx.x < W) cw[threadIdx.x] = c[woff[g] + threadIdx.x];
     __syncthreads();
     if (n >= N) return;
-    float re = 0.f, im = 0.f;
-    for (int w = 0; w < W; ++w) {
-        const float2 t = __ldg(&twM[(mw[w] * n) & (M - 1)]);   // e^{-j 2 pi m n / M}
-        const float2 a = cw[w];
-        // a * conj(t)
-        re = fmaf(a.x, t.x, fmaf(a.y, t.y, re));
-        im = fmaf(a.y, t.x, fmaf(-a.x, t.y, im));
-    }
-    c_hat[g * N + n] = make_float2(re * scale, im * scale);
+    const float2 tz = __ldg(&twM[n & (M - 1)]);
+    const float2 ts = __ldg(&twM[(start[g] * n) & (M - 1)]);
+    const float2 z = make_float2(tz.x, -tz.y), zs = make_float2(ts.x, -ts.y);   // e^{+j 2 pi n / M}, its start-th power
+    float2 acc = cw[W - 1];
+    for (int w = W - 2; w >= 0; --w) acc = cadd(cmul(acc, z), cw[w]);
+    acc = cmul(acc, zs);
+    c_hat[g * N + n] = make_float2(acc.x * scale, acc.y * scale);
 }
 
 constexpr int AL_T = 32;   // targets per tile
@@ -108,7 +104,8 @@ __global__ void __launch_bounds__(256)
 __global__ void __launch_bounds__(256)
     beam_pattern_kernel(const float2 *__restrict__ c_hat, const double *__restrict__ u, int n_dirs, int N, int L,
                         double fc, double fs, double fd, float *__restrict__ pattern) {
-    extern __shared__ float2 ch[];
+    extern __shared__ float2 ch[];   // [N] c_hat, then [n_dirs] Omega / pi as FP32 (hi, lo)
+    float2 *omt = ch + N;
     __shared__ float part[8];
     const int64_t g = blockIdx.x;
     const int s = (int)(g % L);
@@ -126,34 +123,56 @@ __global__ void __launch_bounds__(256)
     for (int w = 0; w < 8; ++w) tot += part[w];
     const float inv = 1.f / (sqrtf(tot) * sqrtf((float)N));
     // subband centre frequency (Eq. SubChannelFreq): fc + ((l - 1/2) / L) fs,
-    // l = s - L/2 + 1, in this order
+    // l = s - L/2 + 1, in this order; Omega / pi = u f / f_d per direction,
+    // formed once per CTA in FP64 and kept as an FP32 (hi, lo) pair (the FP64
+    // pipe is narrow, so the per-lane work below is FP32 only)
     const double f = fc + (((double)(s - L / 2 + 1) - 0.5) / (double)L) * fs;
-    for (int k = warp; k < n_dirs; k += 8) {
+    const double ratio = f / fd;
+    for (int k = threadIdx.x; k < n_dirs; k += 256) {
+        const double om = u[k] * ratio;
+        const float hi = (float)om;
+        omt[k] = make_float2(hi, (float)(om - (double)hi));
+    }
+    __syncthreads();
+    constexpr int DPW = 4;   // directions per warp pass: each shared load feeds four sums
+    for (int k0 = warp * DPW; k0 < n_dirs; k0 += 8 * DPW) {
         // Omega / pi = u f / fd; e^{j Omega n} with n = lane + 32 i.  The two
         // phases (in units of pi) are reduced to [-1, 1] in FP64 before the
         // FP32 sincospi, so their error does not grow with n.
-        const double om = u[k] * (f / fd);
-        double x0 = om * (double)lane, x32 = om * 32.0;
-        x0 -= 2.0 * rint(0.5 * x0);
-        x32 -= 2.0 * rint(0.5 * x32);
-        float s0, c0, s32, c32;
-        sincospif((float)x0, &s0, &c0);
-        sincospif((float)x32, &s32, &c32);
-        float er = c0, ei = s0, re = 0.f, im = 0.f;
+        float er[DPW], ei[DPW], c32[DPW], s32[DPW], re[DPW], im[DPW];
+#pragma unroll
+        for (int d = 0; d < DPW; ++d) {
+            const float2 om = (k0 + d < n_dirs) ? omt[k0 + d] : make_float2(0.f, 0.f);
+            // x0 = om * lane: exact product of the high part (fmaf), reduced
+            // modulo 2 before the low-order terms are added
+            const float p = om.x * (float)lane;
+            const float e = fmaf(om.x, (float)lane, -p) + om.y * (float)lane;
+            const float x0 = (p - 2.f * rintf(0.5f * p)) + e;
+            const float q = om.x * 32.f;   // exact
+            const float x32 = (q - 2.f * rintf(0.5f * q)) + om.y * 32.f;
+            sincospif(x0, &ei[d], &er[d]);
+            sincospif(x32, &s32[d], &c32[d]);
+            re[d] = im[d] = 0.f;
+        }
         for (int n = lane; n < N; n += 32) {
             const float2 a = ch[n];
-            // conj(a) * e
-            re = fmaf(a.x, er, fmaf(a.y, ei, re));
-            im = fmaf(a.x, ei, fmaf(-a.y, er, im));
-            const float nr = er * c32 - ei * s32;
-            ei = fmaf(er, s32, ei * c32);
-            er = nr;
+#pragma unroll
+            for (int d = 0; d < DPW; ++d) {   // conj(a) * e, then e *= e^{j 32 Omega}
+                re[d] = fmaf(a.x, er[d], fmaf(a.y, ei[d], re[d]));
+                im[d] = fmaf(a.x, ei[d], fmaf(-a.y, er[d], im[d]));
+                const float nr = er[d] * c32[d] - ei[d] * s32[d];
+                ei[d] = fmaf(er[d], s32[d], ei[d] * c32[d]);
+                er[d] = nr;
+            }
         }
-        for (int o = 16; o; o >>= 1) {
-            re += __shfl_xor_sync(0xFFFFFFFFu, re, o);
-            im += __shfl_xor_sync(0xFFFFFFFFu, im, o);
+#pragma unroll
+        for (int d = 0; d < DPW; ++d) {
+            for (int o = 16; o; o >>= 1) {
+                re[d] += __shfl_xor_sync(0xFFFFFFFFu, re[d], o);
+                im[d] += __shfl_xor_sync(0xFFFFFFFFu, im[d], o);
+            }
+            if (lane == 0 && k0 + d < n_dirs) pattern[g * n_dirs + k0 + d] = sqrtf(re[d] * re[d] + im[d] * im[d]) * inv;
         }
-        if (lane == 0) pattern[g * n_dirs + k] = sqrtf(re * re + im * im) * inv;
     }
 }
 
@@ -180,7 +199,13 @@ bs_status launch_apply_lifted(const bs_plan *p, const float2 *xc, const float2 *
 bs_status launch_beam_pattern(const bs_plan *p, const float2 *c_hat, int n_dirs, const double *u, float *pattern,
                               cudaStream_t st) {
     if (n_dirs == 0 || p->pairs == 0) return BS_OK;
-    const size_t smem = (size_t)p->cfg.N * sizeof(float2);   // N <= 4096: <= 32 KB
+    const size_t smem = ((size_t)p->cfg.N + n_dirs) * sizeof(float2);
+    if (smem > 200 * 1024) return set_error(BS_EUNSUPPORTED, "beam pattern: N + n_dirs must be <= 25600");
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(beam_pattern_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return cuda_error(e, "beam pattern attribute");
+    }
     beam_pattern_kernel<<<(unsigned)p->pairs, 256, smem, st>>>(c_hat, u, n_dirs, p->cfg.N, p->cfg.L, p->cfg.fc,
                                                               p->cfg.fs, p->cfg.fd, pattern);
     return check_launch("beam pattern launch");
