@@ -75,6 +75,10 @@ _SIGS = {
     "bs_mvdr_solve": ([_P, _P, _P, _P, _P], ctypes.c_int),
     "bs_apply": ([_P, _P, _P, _P, _P], ctypes.c_int),
     "bs_lift": ([_P, _P, _P, _P], ctypes.c_int),
+    # SINR judge, features and loading labels (also used by learned.py)
+    "bs_features": ([_P, _P, _P, _P], ctypes.c_int),
+    "bs_output_sinr": ([_P, _P, _P, _P, _P], ctypes.c_int),
+    "bs_loading_labels": ([_P, _P, ctypes.c_int32, _P, _P, ctypes.c_int32, _P, _P, _P], ctypes.c_int),
     "bs_apply_lifted": ([_P, _P, _P, _P, _P], ctypes.c_int),
     "bs_beam_pattern": ([_P, _P, ctypes.c_int32, _P, _P, _P], ctypes.c_int),
     "bs_run": ([_P, ctypes.POINTER(_Buffers), _P], ctypes.c_int),

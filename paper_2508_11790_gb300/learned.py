@@ -41,9 +41,6 @@ class _Work(ctypes.Structure):
 
 _SIGS = {
     "bs_mlp_param_count": ([ctypes.c_int32] * 3, ctypes.c_int64),
-    "bs_features": ([_P, _P, _P, _P], ctypes.c_int),
-    "bs_output_sinr": ([_P, _P, _P, _P, _P], ctypes.c_int),
-    "bs_loading_labels": ([_P, _P, ctypes.c_int32, _P, _P, ctypes.c_int32, _P, _P, _P], ctypes.c_int),
     "bs_mlp_forward": ([ctypes.POINTER(_Mlp), _P, ctypes.c_int64, _P, ctypes.POINTER(_Work), _P], ctypes.c_int),
     "bs_mlp_train_step": ([ctypes.POINTER(_Mlp), _P, _P, ctypes.c_int64, ctypes.POINTER(_Work), ctypes.c_float, _P,
                            _P], ctypes.c_int),

@@ -38,6 +38,16 @@ def test_every_declared_symbol_is_exported(pkg):
     assert not missing, missing
 
 
+def test_every_declared_function_has_a_ctypes_signature(pkg):
+    """A declared entry point called through ctypes without argtypes would pass
+    64-bit device pointers as 32-bit C ints: every one has a registered
+    signature (the package table, or learned.py's for the network structs)."""
+    from paper_2508_11790_gb300 import learned
+    sigs = set(pkg._SIGS) | set(learned._SIGS)
+    missing = [n for n in declared_functions() if n not in sigs]
+    assert not missing, missing
+
+
 def test_status_strings(pkg):
     L = pkg.lib()
     assert L.bs_status_string(0) == b"ok"
