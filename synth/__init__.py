@@ -11,6 +11,7 @@ from .scene import (
     config_by_name,
     all_configs,
     make_scene,
+    pulse,
     scaled_config,
 )
 
@@ -20,5 +21,6 @@ __all__ = [
     "config_by_name",
     "all_configs",
     "make_scene",
+    "pulse",
     "scaled_config",
 ]

@@ -64,6 +64,11 @@ class SceneConfig:
     sigma2: float = 1.0         # noise variance per element per sample
     delta: float = 10.0         # diagonal loading (10 sigma^2)
     description: str = ""
+    # Coherent pulse train: each target keeps one delay over all test records
+    # and its echo phase advances by 2 pi nu_t per record (nu_t: Doppler in
+    # cycles per record, drawn on the grid k / P_te so that it falls on a
+    # Doppler bin); the default draws an independent delay and phase per record.
+    coherent_targets: bool = False
 
     @property
     def B(self) -> int:
@@ -174,6 +179,8 @@ class Scene:
     u_jam: np.ndarray             # [J] direction sines of the jammers
     jnr_db: np.ndarray            # [J]
     x_interf: Optional[np.ndarray] = None  # [P][F][N] complex64 noise-free jammer part
+    tgt_delay: Optional[np.ndarray] = None    # [T] delays (samples), coherent_targets only
+    tgt_doppler: Optional[np.ndarray] = None  # [T] Doppler bins (cycles per record x P_te)
 
 
 def _directions(g, T, J, N):
@@ -212,6 +219,16 @@ def _plane_wave(theta: np.ndarray, N: int, blk: int = 32) -> np.ndarray:
     return out[..., :N]
 
 
+def pulse(F: int) -> np.ndarray:
+    """The targets' transmitted waveform, [F] complex128: a full-band LFM
+    pulse of Tp = F/2 samples (phase 2 pi (-tau/2 + tau^2 / (2 Tp))), zero
+    after it.  Matched filtering needs its spectrum, an input of the
+    processing after the beamformer."""
+    Tp = max(F // 2, 1)
+    tau = np.arange(F, dtype=np.float64)
+    return np.where(tau < Tp, np.exp(1j * 2 * np.pi * (-0.5 * tau + 0.5 * tau * tau / Tp)), 0.0)
+
+
 def make_scene(cfg: SceneConfig, keep_interference: bool = False,
                k_chunk: int = 64) -> Scene:
     """Synthesise the raw IQ records x[p][t][n] of one workload (seeded)."""
@@ -235,8 +252,17 @@ def make_scene(cfg: SceneConfig, keep_interference: bool = False,
 
     # Target echoes (test records): full-band LFM pulse of F/2 samples, random delay.
     Tp = max(F // 2, 1)
-    delay = g_tgt.integers(0, F - Tp + 1, size=(cfg.P_te, T))
-    psi_t = g_tgt.uniform(0.0, 2 * np.pi, size=(cfg.P_te, T))
+    tgt_delay = tgt_doppler = None
+    if cfg.coherent_targets:
+        tgt_delay = g_tgt.integers(0, F - Tp + 1, size=T)
+        tgt_doppler = g_tgt.integers(0, max(cfg.P_te, 1), size=T)
+        psi0 = g_tgt.uniform(0.0, 2 * np.pi, size=T)
+        delay = np.broadcast_to(tgt_delay, (cfg.P_te, T))
+        rec = np.arange(cfg.P_te, dtype=np.float64)[:, None]
+        psi_t = psi0[None, :] + 2 * np.pi * rec * tgt_doppler[None, :] / max(cfg.P_te, 1)
+    else:
+        delay = g_tgt.integers(0, F - Tp + 1, size=(cfg.P_te, T))
+        psi_t = g_tgt.uniform(0.0, 2 * np.pi, size=(cfg.P_te, T))
     amp_t = math.sqrt(cfg.sigma2 * 10.0 ** (cfg.snr_db / 10.0))
     tau = t[None, None, :] - delay[..., None]
     inside = (tau >= 0) & (tau < Tp)
@@ -282,4 +308,4 @@ def make_scene(cfg: SceneConfig, keep_interference: bool = False,
         for p in range(P):
             x_interf[p] = np.fft.ifft(XJ[p], axis=0, norm="ortho").astype(np.complex64)
     return Scene(cfg=cfg, x=np.ascontiguousarray(x), u_tgt=u_t, u_jam=u_j,
-                 jnr_db=jnr, x_interf=x_interf)
+                 jnr_db=jnr, x_interf=x_interf, tgt_delay=tgt_delay, tgt_doppler=tgt_doppler)
