@@ -408,6 +408,24 @@ def run_ours(args):
                   "beam_pattern_ms": lb["beam_pattern"], "beam_pattern_directions": n_dirs,
                   "beam_pattern_TFLOP/s_fp32": bp_flops / (lb["beam_pattern"] / 1e3) / 1e12}
         del c_hat, out_l, pattern
+    # range-Doppler maps and CFAR of the pass's outputs (rows beyond the hot
+    # path; the synthetic pulse is the scene's)
+    radar = None
+    if rank == 0 and cfg.P_te > 0:
+        from synth import pulse
+        nmap = cfg.T * cfg.P_te * cfg.F
+        pspec = torch.from_numpy(np.fft.fft(pulse(cfg.F), norm="ortho").astype(np.complex64)).to(dev)
+        work = torch.empty(2 * nmap, dtype=torch.complex64, device=dev)
+        rmap = torch.empty(nmap, dtype=torch.float32, device=dev)
+        rfloor = torch.empty(cfg.T, dtype=torch.float32, device=dev)
+        rcount = torch.empty(cfg.T, dtype=torch.int32, device=dev)
+        rmask = torch.empty(nmap, dtype=torch.uint8, device=dev)
+        rb = stage_breakdown([
+            ("range_doppler", lambda: P.bs_range_doppler(plan, b.out, pspec, work, rmap, stream=stream)),
+            ("cfar", lambda: P.bs_cfar(plan, rmap, 10.0, rfloor, rcount, rmask, stream=stream)),
+        ], max(3, args.steps // 4))
+        radar = {"range_doppler_ms": rb["range_doppler"], "cfar_ms": rb["cfar"], "map_cells": nmap}
+        del work, rmap, rmask
     clocks = sampler.stop()
     clocks["window"] = "plain-path, e2e, 1 s load soak, timed and per-stage loops (100 ms samples)"
     info = b.info.cpu().numpy()
@@ -465,7 +483,7 @@ def run_ours(args):
             "autotune": tune,
             "clocks": clocks, "stages": per_stage, "solve_core_ms": solve_core_ms,
             "other_solve_core_ms": other,
-            "plain_fp32": plain, "accuracy": accuracy, "lifted_correlator": lifted,
+            "plain_fp32": plain, "accuracy": accuracy, "lifted_correlator": lifted, "range_doppler": radar,
             "info_counts": {str(k): int(v) for k, v in zip(*np.unique(info, return_counts=True))},
         }
         print(json.dumps(line), flush=True)

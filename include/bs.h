@@ -293,6 +293,29 @@ bs_status bs_apply_lifted(const bs_plan *plan, const bs_cf32 *xc, const bs_cf32 
 bs_status bs_beam_pattern(const bs_plan *plan, const bs_cf32 *c_hat, int32_t n_dirs, const double *u,
                           float *pattern, bs_stream stream);
 
+/* Processing after the beamformer (Sec. II, Fig. 1: synthesis of the
+ * wideband output, then standard range-Doppler processing): for target t,
+ * test record r and FFT bin k, Y[t][r][k] is the beamformed output
+ * out[t L + s][r B + i] of bin q = s B + i, k = (q - F/2) mod F; the matched
+ * filter and the synthesis IFFT (orthonormal) give the range profiles
+ * rp[t][r] = IFFT_k(Y[t][r][k] conj(P[k])), and the Doppler DFT over the
+ * records the power map
+ *   map[t][d][tau] = |sum_r rp[t][r][tau] e^{-j 2 pi d r / P_test}|^2.
+ * out: bs_apply's output [pairs][Vte]; pulse: [F] cf32 orthonormal spectrum
+ * of the transmitted pulse (FFT order); work: caller-owned device scratch of
+ * 2 T P_test F cf32; map: [T][P_test][F] FP32.  F is a power of two in
+ * 16..4096 (plan validation). */
+bs_status bs_range_doppler(const bs_plan *plan, const bs_cf32 *out, const bs_cf32 *pulse, bs_cf32 *work,
+                           float *map, bs_stream stream);
+
+/* CFAR detection (Sec. IV: a threshold above the noise floor, 10 dB in the
+ * paper): floor[t] = mean of map[t] over its P_test F cells (FP32 cells,
+ * compensated sum); a cell is a detection when map > floor * 10^(dB/10),
+ * compared in FP32.  floor: [T] FP32; count: [T] detections; mask (may be
+ * NULL): [T][P_test][F] bytes, 1 for a detection. */
+bs_status bs_cfar(const bs_plan *plan, const float *map, float threshold_db, float *floor, int32_t *count,
+                  uint8_t *mask, bs_stream stream);
+
 /* The whole pass on device buffers: channelise, beamspace, covariance,
  * solve (bs_cov_solve with BS_FLAG_FUSED), apply (delta = plan delta). */
 bs_status bs_run(const bs_plan *plan, const bs_buffers *buf, bs_stream stream);

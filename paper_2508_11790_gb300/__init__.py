@@ -24,7 +24,7 @@ __all__ = [
     "BsError", "Plan", "Buffers", "alloc_buffers", "lib", "bs_plan_tables_host",
     "bs_channelize", "bs_beamspace", "bs_beamspace_full", "bs_window_cov",
     "bs_mvdr_solve", "bs_apply", "bs_run", "bs_run_host",
-    "bs_lift", "bs_apply_lifted", "bs_beam_pattern",
+    "bs_lift", "bs_apply_lifted", "bs_beam_pattern", "bs_range_doppler", "bs_cfar",
 ]
 
 BS_PREC_FP32, BS_PREC_FP16, BS_PREC_BF16 = 0, 1, 2
@@ -81,6 +81,8 @@ _SIGS = {
     "bs_loading_labels": ([_P, _P, ctypes.c_int32, _P, _P, ctypes.c_int32, _P, _P, _P], ctypes.c_int),
     "bs_apply_lifted": ([_P, _P, _P, _P, _P], ctypes.c_int),
     "bs_beam_pattern": ([_P, _P, ctypes.c_int32, _P, _P, _P], ctypes.c_int),
+    "bs_range_doppler": ([_P, _P, _P, _P, _P, _P], ctypes.c_int),
+    "bs_cfar": ([_P, _P, ctypes.c_float, _P, _P, _P, _P], ctypes.c_int),
     "bs_run": ([_P, ctypes.POINTER(_Buffers), _P], ctypes.c_int),
     "bs_run_host": ([_P, _P, _P, ctypes.POINTER(_Buffers), _P], ctypes.c_int),
     "bs_plan_tables_host": ([ctypes.POINTER(_Config), _P, _P], ctypes.c_int),
@@ -413,6 +415,28 @@ def bs_beam_pattern(plan: Plan, c_hat: torch.Tensor, u: torch.Tensor, pattern: t
     _check(lib().bs_beam_pattern(plan.handle, _ptr(c_hat, torch.complex64, s.pairs * plan.N, "c_hat"), n,
                                  _ptr(u, torch.float64, n, "u"), _ptr(pattern, torch.float32, s.pairs * n, "pattern"),
                                  _stream(stream)), "bs_beam_pattern")
+
+
+def bs_range_doppler(plan: Plan, out: torch.Tensor, pulse: torch.Tensor, work: torch.Tensor, rd_map: torch.Tensor,
+                     stream=None):
+    """Range-Doppler power maps [T * P_test * F] (float32) of the beamformed
+    outputs; pulse: [F] complex64 spectrum; work: >= 2 T P_test F complex64."""
+    s = plan.sizes
+    n = plan.T * plan.P_test * plan.F
+    _check(lib().bs_range_doppler(plan.handle, _ptr(out, torch.complex64, s.out_elems, "out"),
+                                  _ptr(pulse, torch.complex64, plan.F, "pulse"),
+                                  _ptr(work, torch.complex64, 2 * n, "work"),
+                                  _ptr(rd_map, torch.float32, n, "map"), _stream(stream)), "bs_range_doppler")
+
+
+def bs_cfar(plan: Plan, rd_map: torch.Tensor, threshold_db: float, floor: torch.Tensor, count: torch.Tensor,
+            mask: Optional[torch.Tensor] = None, stream=None):
+    """CFAR over each target's map: floor [T] float32, count [T] int32,
+    optional mask [T * P_test * F] uint8."""
+    n = plan.T * plan.P_test * plan.F
+    _check(lib().bs_cfar(plan.handle, _ptr(rd_map, torch.float32, n, "map"), float(threshold_db),
+                         _ptr(floor, torch.float32, plan.T, "floor"), _ptr(count, torch.int32, plan.T, "count"),
+                         _ptr(mask, torch.uint8, n, "mask"), _stream(stream)), "bs_cfar")
 
 
 def _cbuf(plan: Plan, b: Buffers) -> _Buffers:

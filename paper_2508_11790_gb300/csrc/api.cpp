@@ -100,6 +100,25 @@ bs_status bs_beam_pattern(const bs_plan *p, const bs_cf32 *c_hat, int32_t n_dirs
     return bs::launch_beam_pattern(p, (const float2 *)c_hat, n_dirs, u, pattern, (cudaStream_t)stream);
 }
 
+bs_status bs_range_doppler(const bs_plan *p, const bs_cf32 *out, const bs_cf32 *pulse, bs_cf32 *work, float *map,
+                           bs_stream stream) {
+    BS_REQUIRE(p, "NULL plan");
+    if (p->Vte == 0) return BS_OK;
+    BS_REQUIRE(out && pulse && work && map, "NULL buffer");
+    if (bs_status s = check_device(p)) return s;
+    return bs::launch_range_doppler(p, (const float2 *)out, (const float2 *)pulse, (float2 *)work, map,
+                                    (cudaStream_t)stream);
+}
+
+bs_status bs_cfar(const bs_plan *p, const float *map, float threshold_db, float *floor, int32_t *count,
+                  uint8_t *mask, bs_stream stream) {
+    BS_REQUIRE(p, "NULL plan");
+    if (p->Vte == 0) return BS_OK;
+    BS_REQUIRE(map && floor && count, "NULL buffer");
+    if (bs_status s = check_device(p)) return s;
+    return bs::launch_cfar(p, map, threshold_db, floor, count, mask, (cudaStream_t)stream);
+}
+
 bs_status bs_cov_solve(const bs_plan *p, const void *z_train, const float *delta_pair, bs_cf64 *R, bs_cf32 *c,
                        int32_t *info, bs_stream stream) {
     BS_REQUIRE(p, "NULL plan");

@@ -210,4 +210,9 @@ bs_status launch_beamspace_full(const bs_plan *p, const float2 *y, int64_t nvec,
     return launch_bs<true, BS_PREC_FP32>(p->cfg.M, y, nvec, p->cfg.N, p->d_twM, yb, ga, st);
 }
 
+bs_status launch_fft_rows(const bs_plan *p, const float2 *y, int64_t nvec, float2 *yb, cudaStream_t st) {
+    GatherArgs ga{};
+    return launch_bs<true, BS_PREC_FP32>(p->cfg.F, y, nvec, p->cfg.F, p->d_twF, yb, ga, st);
+}
+
 }  // namespace bs

@@ -86,6 +86,12 @@ bs_status launch_cov_solve_tables(const void *z, int precision, float store_scal
                                   cudaStream_t st);
 int beamspace_vectors_per_cta(int M);
 bs_status launch_lift(const bs_plan *p, const float2 *c, float2 *c_hat, cudaStream_t st);
+// orthonormal F-point DFT of nvec contiguous rows of F elements (F-point twiddle table)
+bs_status launch_fft_rows(const bs_plan *p, const float2 *y, int64_t nvec, float2 *yb, cudaStream_t st);
+bs_status launch_range_doppler(const bs_plan *p, const float2 *out, const float2 *pulse, float2 *work, float *map,
+                               cudaStream_t st);
+bs_status launch_cfar(const bs_plan *p, const float *map, float threshold_db, float *floor, int32_t *count,
+                      uint8_t *mask, cudaStream_t st);
 bs_status launch_apply_lifted(const bs_plan *p, const float2 *xc, const float2 *c_hat, float2 *out,
                               cudaStream_t st);
 bs_status launch_beam_pattern(const bs_plan *p, const float2 *c_hat, int n_dirs, const double *u, float *pattern,
