@@ -22,3 +22,4 @@ from .beamspace_mvdr import *  # noqa: F401,F403
 from .beamspace_mvdr import __all__  # noqa: F401
 from . import learned_loading  # noqa: E402,F401
 from . import range_doppler  # noqa: E402,F401
+from . import upa  # noqa: E402,F401

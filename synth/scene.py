@@ -69,6 +69,13 @@ class SceneConfig:
     # cycles per record, drawn on the grid k / P_te so that it falls on a
     # Doppler bin); the default draws an independent delay and phase per record.
     coherent_targets: bool = False
+    # Uniform planar array (Eq. ArrayFactor): N = Nx Nz elements ordered
+    # n = n_x Nz + n_z, M = Mx Mz beams ordered m = m_x Mz + m_z, and a
+    # W_x x W_z window per target (W[t] = W_x W_z, Wz[t] = W_z).  Nz = 1 is
+    # the uniform linear array.
+    Nz: int = 1
+    Mz: int = 1
+    Wz: tuple = ()
 
     @property
     def B(self) -> int:
@@ -83,6 +90,19 @@ class SceneConfig:
     def pairs(self) -> int:
         return self.T * self.L
 
+    @property
+    def Nx(self) -> int:
+        return self.N // self.Nz
+
+    @property
+    def Mx(self) -> int:
+        return self.M // self.Mz
+
+    @property
+    def Wz_t(self) -> tuple:
+        """Vertical window size per target (1 for a linear array)."""
+        return tuple(self.Wz) if self.Wz else (1,) * self.T
+
     def validate(self) -> None:
         if self.F % self.L:
             raise ValueError("F must be a multiple of L")
@@ -93,6 +113,11 @@ class SceneConfig:
         kmax = max(self.K) if self.K else 0
         if kmax > self.P_tr * self.B:
             raise ValueError("P_tr * B training vectors cannot cover max(K)")
+        if self.Nz < 1 or self.N % self.Nz or self.Mz < self.Nz or self.M % self.Mz or self.Mx < self.Nx:
+            raise ValueError("planar array: Nz | N, Mz | M, Mz >= Nz, M/Mz >= N/Nz")
+        if len(self.Wz_t) != self.T or any(w % wz or wz > self.Mz or w // wz > self.Mx
+                                           for w, wz in zip(self.W, self.Wz_t)):
+            raise ValueError("planar windows: Wz | W, Wz <= Mz, W/Wz <= M/Mz")
 
 
 def _uniform(name, idx, N, F, L, M, T, W, K, n_jam, jnr_db, P_tr, P_te, desc):
@@ -156,6 +181,13 @@ def scaled_config(cfg: SceneConfig, **changes) -> SceneConfig:
     W or K given as an int is expanded to one entry per target.
     """
     T = changes.get("T", cfg.T)
+    if "Wz" in changes or (cfg.Wz and T != cfg.T):
+        v = changes.get("Wz", cfg.Wz)
+        if isinstance(v, (int, np.integer)):
+            v = (int(v),) * T
+        elif len(v) != T:
+            v = tuple(int(v[i % len(v)]) for i in range(T))
+        changes["Wz"] = tuple(int(a) for a in v)
     for key in ("W", "K"):
         v = changes.get(key, getattr(cfg, key))
         if isinstance(v, (int, np.integer)):
@@ -179,6 +211,8 @@ class Scene:
     u_jam: np.ndarray             # [J] direction sines of the jammers
     jnr_db: np.ndarray            # [J]
     x_interf: Optional[np.ndarray] = None  # [P][F][N] complex64 noise-free jammer part
+    v_tgt: Optional[np.ndarray] = None        # [T] vertical sines sin(theta) (planar arrays)
+    v_jam: Optional[np.ndarray] = None        # [J]
     tgt_delay: Optional[np.ndarray] = None    # [T] delays (samples), coherent_targets only
     tgt_doppler: Optional[np.ndarray] = None  # [T] Doppler bins (cycles per record x P_te)
 
@@ -235,9 +269,21 @@ def make_scene(cfg: SceneConfig, keep_interference: bool = False,
     cfg.validate()
     N, F, P, J, T = cfg.N, cfg.F, cfg.P, cfg.n_jam, cfg.T
     ss = np.random.SeedSequence(cfg.seed)
-    g_geom, g_jam, g_tgt, g_noise = [np.random.default_rng(s) for s in ss.spawn(4)]
+    g_geom, g_jam, g_tgt, g_noise, g_vert = [np.random.default_rng(s) for s in ss.spawn(5)]
 
-    u_t, u_j = _directions(g_geom, T, J, N)
+    u_t, u_j = _directions(g_geom, T, J, cfg.Nx)
+    v_t = v_j = None
+    if cfg.Nz > 1:   # elevations within +-20 deg
+        v_t = np.sin(np.deg2rad(g_vert.uniform(-20.0, 20.0, size=T)))
+        v_j = np.sin(np.deg2rad(g_vert.uniform(-20.0, 20.0, size=J)))
+
+    def response(scale, u, v):
+        """Array response at each bin: [kc][src][N], n = n_x Nz + n_z."""
+        ex = _plane_wave(scale[:, None] * u[None, :], cfg.Nx)
+        if v is None:
+            return ex.astype(np.complex64)
+        ez = _plane_wave(scale[:, None] * v[None, :], cfg.Nz)
+        return (ex[..., :, None] * ez[..., None, :]).reshape(ex.shape[:-1] + (N,)).astype(np.complex64)
     jnr = g_geom.uniform(cfg.jnr_db[0], cfg.jnr_db[1], size=J) if J else np.zeros(0)
 
     t = np.arange(F, dtype=np.float64)
@@ -282,12 +328,12 @@ def make_scene(cfg: SceneConfig, keep_interference: bool = False,
         k1 = min(F, k0 + k_chunk)
         scale = np.pi * (cfg.fc + f_bin[k0:k1]) / cfg.fd           # [kc]
         # true-time-delay response of each source at each bin: [kc][src][N]
-        Ej = _plane_wave(scale[:, None] * u_j[None, :], N).astype(np.complex64)
+        Ej = response(scale, u_j, v_j)
         xj = np.matmul(SJ[k0:k1], Ej)                               # [kc][P][N]
         if XJ is not None:
             XJ[:, k0:k1, :] = xj.transpose(1, 0, 2)
         if T and cfg.P_te:
-            Et = _plane_wave(scale[:, None] * u_t[None, :], N).astype(np.complex64)
+            Et = response(scale, u_t, v_t)
             xj[:, cfg.P_tr:, :] += np.matmul(ST[k0:k1], Et)         # [kc][P_te][N]
         X[:, k0:k1, :] = xj.transpose(1, 0, 2)
 
@@ -308,4 +354,5 @@ def make_scene(cfg: SceneConfig, keep_interference: bool = False,
         for p in range(P):
             x_interf[p] = np.fft.ifft(XJ[p], axis=0, norm="ortho").astype(np.complex64)
     return Scene(cfg=cfg, x=np.ascontiguousarray(x), u_tgt=u_t, u_jam=u_j,
-                 jnr_db=jnr, x_interf=x_interf, tgt_delay=tgt_delay, tgt_doppler=tgt_doppler)
+                 jnr_db=jnr, x_interf=x_interf, v_tgt=v_t, v_jam=v_j, tgt_delay=tgt_delay,
+                 tgt_doppler=tgt_doppler)
