@@ -100,6 +100,18 @@ typedef struct {
     double kappa_max;    /* FP64 escalation threshold on the Cholesky pivot
                             ratio (max L_ii / min L_ii)^2; <= 0 selects 1e5 */
     float store_scale;   /* 16-bit windows hold value * store_scale (<= 0: 1) */
+    /* Uniform planar array (Eq. ArrayFactor, Eq. OverallDFT, Eq. OverallWindow);
+     * Nz <= 1 (with Mz <= 1, Wz and v NULL) is the linear array above.
+     * Elements n = n_x Nz + n_z (N = Nx Nz), beams m = m_x Mz + m_z
+     * (M = Mx Mz), window entries w = w_x Wz + w_z (W = Wx Wz, the selector
+     * read as S_h (x) S_v).  u[t] = cos(theta) sin(phi) (horizontal),
+     * v[t] = sin(theta) (vertical).  Planar plans need N <= 1024 and
+     * M <= 2048; bs_lift, bs_beam_pattern and bs_beamspace_full are
+     * linear-array only. */
+    int32_t Nz;          /* vertical elements (0 or 1: linear array) */
+    int32_t Mz;          /* vertical FFT size, power of 2, Nz <= Mz */
+    const int32_t *Wz;   /* [T] host: vertical window size per target, dividing W[t] */
+    const double  *v;    /* [T] host: vertical direction sine sin(theta) per target */
 } bs_config;
 
 typedef struct {

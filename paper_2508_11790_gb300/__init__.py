@@ -45,6 +45,8 @@ class _Config(ctypes.Structure):
         ("W", ctypes.POINTER(ctypes.c_int32)), ("K", ctypes.POINTER(ctypes.c_int32)),
         ("delta", ctypes.c_double), ("precision", ctypes.c_int32), ("flags", ctypes.c_uint32),
         ("kappa_max", ctypes.c_double), ("store_scale", ctypes.c_float),
+        ("Nz", ctypes.c_int32), ("Mz", ctypes.c_int32),
+        ("Wz", ctypes.POINTER(ctypes.c_int32)), ("v", ctypes.POINTER(ctypes.c_double)),
     ]
 
 
@@ -164,17 +166,23 @@ class Sizes:
 
 
 def _make_config(N, F, L, M, u, W, K, P_train, P_test, fc, fs, fd, delta, precision=BS_PREC_FP32,
-                 flags=0, kappa_max=0.0, store_scale=0.0):
-    """ctypes config plus the numpy arrays it points into (keep both alive)."""
+                 flags=0, kappa_max=0.0, store_scale=0.0, Nz=1, Mz=1, Wz=None, v=None):
+    """ctypes config plus the numpy arrays it points into (keep both alive).
+    Nz > 1 (with Mz, per-target Wz and vertical sines v) makes it planar."""
     ua = np.ascontiguousarray(u, dtype=np.float64)
     Wa = np.ascontiguousarray(W, dtype=np.int32)
     Ka = np.ascontiguousarray(K, dtype=np.int32)
+    planar = Nz > 1 or Mz > 1
+    Wza = np.ascontiguousarray(Wz if Wz is not None else np.ones(len(ua)), dtype=np.int32)
+    va = np.ascontiguousarray(v if v is not None else np.zeros(len(ua)), dtype=np.float64)
     cfg = _Config(N, F, L, M, len(ua), P_train, P_test, fc, fs, fd,
                   ua.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                   Wa.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                   Ka.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
-                  delta, precision, flags, kappa_max, store_scale)
-    return cfg, (ua, Wa, Ka)
+                  delta, precision, flags, kappa_max, store_scale, Nz, Mz,
+                  Wza.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)) if planar else None,
+                  va.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if planar else None)
+    return cfg, (ua, Wa, Ka, Wza, va)
 
 
 def bs_plan_tables_host(**kw):
@@ -196,10 +204,13 @@ class Plan:
                  W: Sequence[int], K: Sequence[int], P_train: int, P_test: int,
                  fc: float, fs: float, fd: float, delta: float,
                  precision: int = BS_PREC_FP32, flags: int = 0,
-                 kappa_max: float = 0.0, store_scale: float = 0.0):
+                 kappa_max: float = 0.0, store_scale: float = 0.0,
+                 Nz: int = 1, Mz: int = 1, Wz: Optional[Sequence[int]] = None,
+                 v: Optional[Sequence[float]] = None):
         self.T = len(u)
         cfg, self._keep = _make_config(N, F, L, M, u, W, K, P_train, P_test, fc, fs, fd, delta,
-                                       precision, flags, kappa_max, store_scale)
+                                       precision, flags, kappa_max, store_scale, Nz, Mz, Wz, v)
+        self.Nz, self.Mz = Nz, Mz
         self.N, self.F, self.L, self.M = N, F, L, M
         self.P_train, self.P_test = P_train, P_test
         self.precision, self.flags = precision, flags
@@ -211,8 +222,12 @@ class Plan:
         self.sizes = Sizes(**{f: getattr(s, f) for f, _ in _Sizes._fields_})
 
     @classmethod
-    def from_scene_config(cls, cfg, u, precision=BS_PREC_FP32, flags=0, **kw):
-        """Plan for a ``synth.SceneConfig`` workload with target sines u."""
+    def from_scene_config(cls, cfg, u, precision=BS_PREC_FP32, flags=0, v=None, **kw):
+        """Plan for a ``synth.SceneConfig`` workload with target sines u (and,
+        for a planar array, vertical sines v)."""
+        planar = getattr(cfg, "Nz", 1) > 1
+        if planar:
+            kw.update(Nz=cfg.Nz, Mz=cfg.Mz, Wz=cfg.Wz_t, v=v)
         return cls(N=cfg.N, F=cfg.F, L=cfg.L, M=cfg.M, u=u, W=cfg.W, K=cfg.K,
                    P_train=cfg.P_tr, P_test=cfg.P_te, fc=cfg.fc, fs=cfg.fs, fd=cfg.fd,
                    delta=cfg.delta, precision=precision, flags=flags, **kw)

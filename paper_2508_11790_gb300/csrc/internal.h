@@ -25,6 +25,11 @@ struct bs_plan {
     std::vector<double> u;              // per target
     // per pair (g = t * L + s)
     std::vector<int32_t> start, Wg, Kg;
+    // planar arrays: vertical window start per pair, vertical window per target
+    bool planar = false;
+    int Nx = 0, Nz = 1, Mx = 0, Mz = 1;
+    std::vector<int32_t> start_z, Wzt;
+    int32_t *d_start_z = nullptr, *d_Wz = nullptr;
     std::vector<int64_t> woff, ztr_off, zte_off, roff;   // pairs + 1 entries
     std::vector<bs_cf64> at;                              // windowed steering, woff-packed
     int64_t ztr_elems = 0, zte_elems = 0, r_elems = 0, c_elems = 0;

@@ -76,6 +76,41 @@ static bs_cf64 windowed_steering(double omega, int N, int M, int m) {
     return bs_cf64{amp * std::cos(ph) * sc, amp * std::sin(ph) * sc};
 }
 
+// Array geometry: linear (Nz = Mz = 1) or planar (Nx x Nz elements,
+// Mx x Mz beams).
+struct Geom {
+    bool planar;
+    int Nx, Nz, Mx, Mz;
+};
+static Geom geometry(const bs_config &c) {
+    Geom g;
+    g.planar = c.Nz > 1 || c.Mz > 1;
+    g.Nz = g.planar ? std::max(c.Nz, 1) : 1;
+    g.Mz = g.planar ? std::max(c.Mz, 1) : 1;
+    g.Nx = c.N / g.Nz;
+    g.Mx = c.M / g.Mz;
+    return g;
+}
+
+// Window starts of pair (t, s): each axis centred on its own squinted spatial
+// frequency (Eq. OverallWindow per axis); sz = 0 for a linear array.
+static void pair_starts(const bs_config &c, const Geom &G, int t, int s, int *sx, int *sz) {
+    const int Wz = G.planar ? c.Wz[t] : 1;
+    *sx = window_start(c.u[t], s, c.W[t] / Wz, c.L, G.Mx, c.fc, c.fs, c.fd);
+    *sz = G.planar ? window_start(c.v[t], s, Wz, c.L, G.Mz, c.fc, c.fs, c.fd) : 0;
+}
+
+// Entry w = w_x Wz + w_z of the windowed steering vector S D a: the product
+// of the two axes' closed forms (S D a = (S_h D_h^T a_x) (x) (S_v D_v a_z)).
+static bs_cf64 pair_steering(const bs_config &c, const Geom &G, int t, int s, int sx, int sz, int w) {
+    const double ratio = subband_freq(s, c.L, c.fc, c.fs) / c.fd;
+    const int Wz = G.planar ? c.Wz[t] : 1;
+    const bs_cf64 ax = windowed_steering(M_PI * c.u[t] * ratio, G.Nx, G.Mx, (sx + w / Wz) % G.Mx);
+    if (!G.planar) return ax;
+    const bs_cf64 az = windowed_steering(M_PI * c.v[t] * ratio, G.Nz, G.Mz, (sz + w % Wz) % G.Mz);
+    return bs_cf64{ax.re * az.re - ax.im * az.im, ax.re * az.im + ax.im * az.re};
+}
+
 template <class T>
 static bs_status upload(T **dst, const std::vector<T> &src) {
     if (src.empty()) return BS_OK;
@@ -118,6 +153,8 @@ void bs_plan_destroy(bs_plan *p) {
     cudaFree(p->d_Kg);
     cudaFree(p->d_gather);
     cudaFree(p->d_gsub);
+    cudaFree(p->d_start_z);
+    cudaFree(p->d_Wz);
     cudaFree(p->d_woff);
     cudaFree(p->d_ztr_off);
     cudaFree(p->d_zte_off);
@@ -154,6 +191,19 @@ static bs_status validate_config(const bs_config *cfg) {
     if (c.precision < BS_PREC_FP32 || c.precision > BS_PREC_BF16)
         return set_error(BS_EINVAL, "unknown precision");
     const int B = c.F / c.L;
+    if (c.Nz > 1 || c.Mz > 1) {
+        if (c.Nz < 1 || c.N % c.Nz) return set_error(BS_EINVAL, "planar: Nz must divide N");
+        if (!is_pow2(c.Mz) || c.Mz < c.Nz || c.M % c.Mz || c.M / c.Mz < c.N / c.Nz)
+            return set_error(BS_EINVAL, "planar: Mz a power of two, Nz <= Mz, N/Nz <= M/Mz");
+        if (c.N > 1024 || c.M > 2048) return set_error(BS_EUNSUPPORTED, "planar: N <= 1024 and M <= 2048");
+        if (!c.Wz || !c.v) return set_error(BS_EINVAL, "planar: Wz and v must be given");
+        for (int t = 0; t < c.T; ++t) {
+            if (c.Wz[t] < 1 || c.W[t] % c.Wz[t] || c.Wz[t] > c.Mz || c.W[t] / c.Wz[t] > c.M / c.Mz)
+                return set_error(BS_EINVAL, "planar: Wz must divide W, Wz <= Mz, W/Wz <= M/Mz");
+            if (!std::isfinite(c.v[t]) || std::fabs(c.v[t]) > 1.0)
+                return set_error(BS_EINVAL, "direction sines must lie in [-1, 1]");
+        }
+    }
     for (int t = 0; t < c.T; ++t) {
         if (c.W[t] < 1 || c.W[t] > 16) return set_error(BS_EUNSUPPORTED, "window sizes must be in 1..16");
         if (c.W[t] > c.M) return set_error(BS_EINVAL, "window larger than M");
@@ -168,16 +218,16 @@ static bs_status validate_config(const bs_config *cfg) {
 bs_status bs_plan_tables_host(const bs_config *cfg, int32_t *start, bs_cf64 *a_tilde) {
     if (bs_status st = validate_config(cfg)) return st;
     const bs_config &c = *cfg;
+    const Geom G = geometry(c);
     int64_t e = 0;
     for (int t = 0; t < c.T; ++t) {
         for (int s = 0; s < c.L; ++s) {
             const int64_t g = (int64_t)t * c.L + s;
-            const int W = c.W[t];
-            const int st = window_start(c.u[t], s, W, c.L, c.M, c.fc, c.fs, c.fd);
-            if (start) start[g] = st;
-            const double omega = M_PI * c.u[t] * (subband_freq(s, c.L, c.fc, c.fs) / c.fd);
-            for (int w = 0; w < W; ++w, ++e)
-                if (a_tilde) a_tilde[e] = windowed_steering(omega, c.N, c.M, (st + w) % c.M);
+            int sx, sz;
+            pair_starts(c, G, t, s, &sx, &sz);
+            if (start) start[g] = sx;
+            for (int w = 0; w < c.W[t]; ++w, ++e)
+                if (a_tilde) a_tilde[e] = pair_steering(c, G, t, s, sx, sz, w);
         }
     }
     return BS_OK;
@@ -194,6 +244,16 @@ bs_status bs_plan_create(bs_plan **out, const bs_config *cfg) {
     p->cfg.u = nullptr;
     p->cfg.W = nullptr;
     p->cfg.K = nullptr;
+    p->cfg.Wz = nullptr;
+    p->cfg.v = nullptr;
+    const Geom geo = geometry(c);
+    p->planar = geo.planar;
+    p->Nx = geo.Nx;
+    p->Nz = geo.Nz;
+    p->Mx = geo.Mx;
+    p->Mz = geo.Mz;
+    p->Wzt.assign((size_t)c.T, 1);
+    if (geo.planar) p->Wzt.assign(c.Wz, c.Wz + c.T);
     if (!(p->cfg.kappa_max > 0)) p->cfg.kappa_max = 1e5;
     if (!(p->cfg.store_scale > 0)) p->cfg.store_scale = 1.0f;
     p->B = B;
@@ -210,6 +270,7 @@ bs_status bs_plan_create(bs_plan **out, const bs_config *cfg) {
     }
     const int64_t G = p->pairs;
     p->start.resize(G);
+    p->start_z.resize(G);
     p->Wg.resize(G);
     p->Kg.resize(G);
     p->woff.assign(G + 1, 0);
@@ -222,7 +283,10 @@ bs_status bs_plan_create(bs_plan **out, const bs_config *cfg) {
             const int W = p->Wt[t], K = p->Kt[t];
             p->Wg[g] = W;
             p->Kg[g] = K;
-            p->start[g] = window_start(p->u[t], s, W, c.L, c.M, c.fc, c.fs, c.fd);
+            int sx, sz;
+            pair_starts(c, geo, t, s, &sx, &sz);
+            p->start[g] = sx;
+            p->start_z[g] = sz;
             p->woff[g + 1] = p->woff[g] + W;
             p->ztr_off[g + 1] = p->ztr_off[g] + (int64_t)W * K;
             p->zte_off[g + 1] = p->zte_off[g] + (int64_t)W * p->Vte;
@@ -239,10 +303,8 @@ bs_status bs_plan_create(bs_plan **out, const bs_config *cfg) {
     for (int t = 0; t < c.T; ++t) {
         for (int s = 0; s < c.L; ++s) {
             const int64_t g = (int64_t)t * c.L + s;
-            const double omega = M_PI * p->u[t] * (subband_freq(s, c.L, c.fc, c.fs) / c.fd);
             for (int w = 0; w < p->Wg[g]; ++w) {
-                const int m = (p->start[g] + w) % c.M;
-                const bs_cf64 a = windowed_steering(omega, c.N, c.M, m);
+                const bs_cf64 a = pair_steering(c, geo, t, s, p->start[g], p->start_z[g], w);
                 const int64_t e = p->woff[g] + w;
                 p->at[e] = a;
                 at32[e] = make_float2((float)a.re, (float)a.im);
@@ -285,6 +347,8 @@ bs_status bs_plan_create(bs_plan **out, const bs_config *cfg) {
     if (!st) st = upload(&p->d_Kg, p->Kg);
     if (!st) st = upload(&p->d_gather, p->gather);
     if (!st) st = upload(&p->d_gsub, p->gsub);
+    if (!st) st = upload(&p->d_start_z, p->start_z);
+    if (!st) st = upload(&p->d_Wz, p->Wzt);
     if (!st) st = upload(&p->d_woff, p->woff);
     if (!st) st = upload(&p->d_ztr_off, p->ztr_off);
     if (!st) st = upload(&p->d_zte_off, p->zte_off);

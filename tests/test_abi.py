@@ -109,3 +109,32 @@ def test_window_ties_round_up(pkg):
     for t in range(3):
         for s in range(L):
             assert start[t * L + s] == O.window_start(u[t], s, kw["W"][t], L, M, fc, fs, fd)
+
+
+def test_planar_window_tables_match_oracle(pkg):
+    """Planar plans: horizontal window starts and the windowed steering
+    vectors (Kronecker of the two axes) computed by the library on the host
+    equal the planar oracle's."""
+    from oracle import upa as U
+    from synth import scaled_config
+    cfg = scaled_config(all_configs()["C1"], name="upa-tables", N=128, Nz=4, M=512, Mz=8, T=5,
+                        W=(8, 16, 4, 2, 6), Wz=(2, 4, 4, 1, 3), K=40, P_tr=2, P_te=1)
+    sc = make_scene(cfg)
+    start, at = pkg.bs_plan_tables_host(N=cfg.N, F=cfg.F, L=cfg.L, M=cfg.M, u=sc.u_tgt, W=cfg.W, K=cfg.K,
+                                        P_train=cfg.P_tr, P_test=cfg.P_te, fc=cfg.fc, fs=cfg.fs, fd=cfg.fd,
+                                        delta=cfg.delta, Nz=cfg.Nz, Mz=cfg.Mz, Wz=cfg.Wz_t, v=sc.v_tgt)
+    D = U.dft2d(cfg.Mx, cfg.Nx, cfg.Mz, cfg.Nz)
+    e = 0
+    for t in range(cfg.T):
+        Wz = cfg.Wz_t[t]
+        Wx = cfg.W[t] // Wz
+        for s in range(cfg.L):
+            f = O.subband_center_freq(s, cfg.L, cfg.fc, cfg.fs)
+            sx = O.window_start(float(sc.u_tgt[t]), s, Wx, cfg.L, cfg.Mx, cfg.fc, cfg.fs, cfg.fd)
+            sz = O.window_start(float(sc.v_tgt[t]), s, Wz, cfg.L, cfg.Mz, cfg.fc, cfg.fs, cfg.fd)
+            assert start[t * cfg.L + s] == sx
+            beams = U.window_beams2d(sx, Wx, cfg.Mx, sz, Wz, cfg.Mz)
+            a = D[beams] @ U.steering2d(O.squinted_omega(float(sc.u_tgt[t]), f, cfg.fd),
+                                        O.squinted_omega(float(sc.v_tgt[t]), f, cfg.fd), cfg.Nx, cfg.Nz)
+            np.testing.assert_allclose(at[e:e + cfg.W[t]], a, atol=1e-12)
+            e += cfg.W[t]
