@@ -43,6 +43,7 @@ bs_status bs_beamspace(const bs_plan *p, const bs_cf32 *xc, void *z_train, bs_cf
 
 bs_status bs_beamspace_full(const bs_plan *p, const bs_cf32 *y, int64_t nvec, bs_cf32 *yb, bs_stream stream) {
     BS_REQUIRE(p, "NULL plan");
+    if (p->planar) return set_error(BS_EUNSUPPORTED, "bs_beamspace_full: linear arrays only");
     BS_REQUIRE(nvec >= 0, "nvec must be >= 0");
     if (nvec == 0) return BS_OK;
     BS_REQUIRE(y && yb, "NULL buffer");
@@ -75,6 +76,7 @@ bs_status bs_apply(const bs_plan *p, const bs_cf32 *z_test, const bs_cf32 *c, bs
 
 bs_status bs_lift(const bs_plan *p, const bs_cf32 *c, bs_cf32 *c_hat, bs_stream stream) {
     BS_REQUIRE(p, "NULL plan");
+    if (p->planar) return set_error(BS_EUNSUPPORTED, "bs_lift: linear arrays only");
     BS_REQUIRE(c && c_hat, "NULL buffer");
     if (bs_status s = check_device(p)) return s;
     return bs::launch_lift(p, (const float2 *)c, (float2 *)c_hat, (cudaStream_t)stream);
@@ -83,6 +85,7 @@ bs_status bs_lift(const bs_plan *p, const bs_cf32 *c, bs_cf32 *c_hat, bs_stream 
 bs_status bs_apply_lifted(const bs_plan *p, const bs_cf32 *xc, const bs_cf32 *c_hat, bs_cf32 *out,
                           bs_stream stream) {
     BS_REQUIRE(p, "NULL plan");
+    if (p->planar) return set_error(BS_EUNSUPPORTED, "bs_apply_lifted: linear arrays only");
     if (p->Vte == 0) return BS_OK;
     BS_REQUIRE(xc && c_hat && out, "NULL buffer");
     if (bs_status s = check_device(p)) return s;
@@ -93,6 +96,7 @@ bs_status bs_apply_lifted(const bs_plan *p, const bs_cf32 *xc, const bs_cf32 *c_
 bs_status bs_beam_pattern(const bs_plan *p, const bs_cf32 *c_hat, int32_t n_dirs, const double *u, float *pattern,
                           bs_stream stream) {
     BS_REQUIRE(p, "NULL plan");
+    if (p->planar) return set_error(BS_EUNSUPPORTED, "bs_beam_pattern: linear arrays only");
     BS_REQUIRE(n_dirs >= 0, "n_dirs must be >= 0");
     if (n_dirs == 0) return BS_OK;
     BS_REQUIRE(c_hat && u && pattern, "NULL buffer");

@@ -194,6 +194,7 @@ bs_status launch_beamspace(const bs_plan *p, const float2 *xc, void *ztr, float2
     ga.ztr = ztr;
     ga.zte = zte;
     ga.store_scale = p->cfg.store_scale;
+    if (p->planar) return launch_beamspace2d(p, xc, ga, st);
     bool used = false;
     const bs_status s = launch_beamspace_tma(p, xc, ga, st, &used);
     if (s || used) return s;

@@ -76,5 +76,7 @@ __device__ __forceinline__ void fill_target_entry(const GatherArgs &ga, int t, i
 // groups of vpb vectors crossing a subband, or BS_FLAG_NO_TMA).
 bs_status launch_beamspace_tma(const bs_plan *p, const float2 *xc, const GatherArgs &ga, cudaStream_t st,
                                bool *used);
+// Planar arrays (beamspace2d.cu): 2-D transform and Wx x Wz window gather.
+bs_status launch_beamspace2d(const bs_plan *p, const float2 *xc, const GatherArgs &ga, cudaStream_t st);
 
 }  // namespace bs
