@@ -76,6 +76,8 @@ typedef enum {
 #define BS_FLAG_NO_TMA     (1u << 3) /* channeliser without the TMA-staged persistent kernel */
 #define BS_FLAG_FUSED      (1u << 4) /* bs_run: bs_cov_solve instead of bs_window_cov + bs_mvdr_solve */
 #define BS_FLAG_SIMT_COV   (1u << 5) /* 16-bit windows: FP32 SIMT products instead of the tensor cores */
+#define BS_FLAG_STAGED_FFT (1u << 6) /* beamspace at M = 1024..4096, N <= 1024: the bulk-copy-staged
+                                        Stockham kernel instead of the warp-per-transform kernel */
 
 typedef struct { float re, im; } bs_cf32;
 typedef struct { double re, im; } bs_cf64;

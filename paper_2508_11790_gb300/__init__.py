@@ -20,6 +20,7 @@ from .build import lib_path
 __all__ = [
     "BS_PREC_FP32", "BS_PREC_FP16", "BS_PREC_BF16",
     "BS_FLAG_PLAIN", "BS_FLAG_NO_REFINE", "BS_FLAG_NO_FP64", "BS_FLAG_NO_TMA", "BS_FLAG_FUSED", "BS_FLAG_SIMT_COV",
+    "BS_FLAG_STAGED_FFT",
     "bs_cov_solve", "bs_autotune", "bs_set_launch", "Graph", "bs_cov_solve_noalloc",
     "BsError", "Plan", "Buffers", "alloc_buffers", "lib", "bs_plan_tables_host",
     "bs_channelize", "bs_beamspace", "bs_beamspace_full", "bs_window_cov",
@@ -30,6 +31,7 @@ __all__ = [
 BS_PREC_FP32, BS_PREC_FP16, BS_PREC_BF16 = 0, 1, 2
 BS_FLAG_PLAIN, BS_FLAG_NO_REFINE, BS_FLAG_NO_FP64, BS_FLAG_NO_TMA, BS_FLAG_FUSED = 1, 2, 4, 8, 16
 BS_FLAG_SIMT_COV = 32
+BS_FLAG_STAGED_FFT = 64
 
 
 class BsError(RuntimeError):

@@ -48,6 +48,14 @@ __device__ __forceinline__ void store_train(void *z, int64_t idx, float2 v, floa
 
 constexpr int kTabT = 256;   // targets whose gather entries are staged in shared memory
 
+// Gather entry of one target for the current vector or group (16 bytes: one
+// shared-memory load): window-array base, start | (W << 16), output count.
+struct __align__(16) GatherEnt {
+    long long base;
+    int sw;
+    int n;
+};
+
 // Gather entry of target t for a CTA at subband s whose first vector is v0:
 // base element offset in the window array, start | (W << 16), output count.
 __device__ __forceinline__ void fill_target_entry(const GatherArgs &ga, int t, int s, int v0, int nv,
@@ -76,6 +84,11 @@ __device__ __forceinline__ void fill_target_entry(const GatherArgs &ga, int t, i
 // groups of vpb vectors crossing a subband, or BS_FLAG_NO_TMA).
 bs_status launch_beamspace_tma(const bs_plan *p, const float2 *xc, const GatherArgs &ga, cudaStream_t st,
                                bool *used);
+// Warp-per-transform variant (beamspace_warp.cu) for M = 1024, 2048, 4096
+// and N <= 1024; *used = false for other plans, more than kTabT targets,
+// BS_FLAG_STAGED_FFT or BS_FLAG_NO_TMA.
+bs_status launch_beamspace_warp(const bs_plan *p, const float2 *xc, const GatherArgs &ga, cudaStream_t st,
+                                bool *used);
 // Planar arrays (beamspace2d.cu): 2-D transform and Wx x Wz window gather.
 bs_status launch_beamspace2d(const bs_plan *p, const float2 *xc, const GatherArgs &ga, cudaStream_t st);
 

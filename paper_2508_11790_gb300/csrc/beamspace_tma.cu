@@ -36,14 +36,6 @@ namespace bs {
 
 constexpr int kGatherRegs = 8;   // gather entries per thread held in registers
 
-// Gather entry of one target for the current group (16 bytes: one
-// shared-memory load): window-array base, start | (W << 16), output count.
-struct __align__(16) GatherEnt {
-    long long base;
-    int sw;
-    int n;
-};
-
 template <int M>
 struct BsTmaCfg {
     using RP = Radix<M>;

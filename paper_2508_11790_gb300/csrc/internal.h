@@ -36,6 +36,7 @@ struct bs_plan {
     // beamspace gather: vectors per CTA and the (target, k) table of one CTA
     int vpb = 0;
     std::vector<int32_t> gather;        // [vpb * sumW]: (t << 8) | (c << 4) | w, target-major
+    std::vector<int32_t> glist;         // [sumW]: (t << 8) | w, target-major (one vector)
     // per (subband, target), subband-major: {ztr_off, zte_off, start | W << 16, K}
     std::vector<int64_t> gsub;
     // device copies
@@ -43,6 +44,7 @@ struct bs_plan {
     int32_t *d_start = nullptr, *d_Wg = nullptr, *d_Kg = nullptr, *d_gather = nullptr;
     int64_t *d_woff = nullptr, *d_ztr_off = nullptr, *d_zte_off = nullptr, *d_roff = nullptr;
     int64_t *d_gsub = nullptr;
+    int32_t *d_glist = nullptr;
     float2 *d_at32 = nullptr;
     float2 *d_atlo = nullptr;                    // a~ - (float)a~ (double-float low parts)
     double2 *d_at64 = nullptr;

@@ -153,6 +153,7 @@ void bs_plan_destroy(bs_plan *p) {
     cudaFree(p->d_Kg);
     cudaFree(p->d_gather);
     cudaFree(p->d_gsub);
+    cudaFree(p->d_glist);
     cudaFree(p->d_start_z);
     cudaFree(p->d_Wz);
     cudaFree(p->d_woff);
@@ -320,6 +321,9 @@ bs_status bs_plan_create(bs_plan **out, const bs_config *cfg) {
     for (int t = 0; t < c.T; ++t)
         for (int cc = 0; cc < p->vpb; ++cc)
             for (int w = 0; w < p->Wt[t]; ++w) p->gather.push_back((t << 8) | (cc << 4) | w);
+    p->glist.reserve((size_t)p->sumW);
+    for (int t = 0; t < c.T; ++t)
+        for (int w = 0; w < p->Wt[t]; ++w) p->glist.push_back((t << 8) | w);
     // the same per-pair fields subband-major, so that the per-group entries
     // of consecutive targets are one contiguous read
     p->gsub.resize((size_t)4 * G);
@@ -347,6 +351,7 @@ bs_status bs_plan_create(bs_plan **out, const bs_config *cfg) {
     if (!st) st = upload(&p->d_Kg, p->Kg);
     if (!st) st = upload(&p->d_gather, p->gather);
     if (!st) st = upload(&p->d_gsub, p->gsub);
+    if (!st) st = upload(&p->d_glist, p->glist);
     if (!st) st = upload(&p->d_start_z, p->start_z);
     if (!st) st = upload(&p->d_Wz, p->Wzt);
     if (!st) st = upload(&p->d_woff, p->woff);

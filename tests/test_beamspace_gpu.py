@@ -1,6 +1,7 @@
 """GPU parity of the window beamspace stage (bs_beamspace) for the
-three-pass sizes M = 512 .. 4096, which the persistent bulk-copy kernel
-serves, and of the one-shot kernel it stands in for (BS_FLAG_NO_TMA):
+three-pass sizes M = 512 .. 4096: the warp-per-transform kernel (M = 1024,
+2048, 4096 with N <= 1024), the persistent bulk-copy kernel (the other
+sizes, and BS_FLAG_STAGED_FFT) and the one-shot kernel (BS_FLAG_NO_TMA):
 every training and test window against the oracle's zero-padded DFT
 (Eq. VerDFT, Eq. BeamTransform) and window selection (Eq. OverallWindow,
 Eq. ApplyWindow) of the same channelised input.
@@ -75,6 +76,9 @@ CASES = [
     (400, 1024, 1024, 32, 3, 1, [11, 2], [64, 95]),
     (2000, 4096, 256, 16, 2, 1, [9, 13], [32, 7]),
     (4096, 4096, 128, 8, 2, 0, [6], [20]),
+    (1024, 4096, 256, 16, 2, 1, [9, 16, 2], [32, 17, 3]),
+    (700, 4096, 256, 16, 3, 2, [5, 12], [48, 40]),
+    (1000, 1024, 512, 32, 2, 1, [15, 4], [9, 32]),
 ]
 
 
@@ -92,25 +96,49 @@ def test_window_beamspace(case, precision):
     _check_windows(plan, off, ztr, zte, xc, M, L, Ptr, Pte, precision)
 
 
-@pytest.mark.parametrize("case", CASES[:3], ids=[f"N{c[0]}_M{c[1]}" for c in CASES[:3]])
-def test_persistent_matches_one_shot_kernel(case):
-    """The persistent kernel and the one-shot kernel (BS_FLAG_NO_TMA) read
-    their twiddles differently (per-thread table values against products
-    of table values) but agree to within twice the FFT bound; the one-shot
-    kernel meets the oracle bound on its own."""
+KERNEL_CASES = CASES[:3] + CASES[-3:]
+
+
+@pytest.mark.parametrize("case", KERNEL_CASES, ids=[f"N{c[0]}_M{c[1]}" for c in KERNEL_CASES])
+def test_kernels_agree(case):
+    """The default kernel (warp-per-transform where it applies), the
+    bulk-copy-staged kernel (BS_FLAG_STAGED_FFT) and the one-shot kernel
+    (BS_FLAG_NO_TMA) factor the transform differently and read their
+    twiddles differently (table values, products of table values, folded
+    constants) but agree to within twice the FFT bound; each meets the
+    oracle bound on its own."""
     N, M, F, L, Ptr, Pte, W, K = case
     rng = np.random.default_rng(5 + N)
     Pn = Ptr + Pte
     xc = (rng.standard_normal((Pn, F, N)) + 1j * rng.standard_normal((Pn, F, N))).astype(np.complex64)
     u = list(rng.uniform(-0.9, 0.9, size=len(W)))
     outs = []
-    for flags in (0, P.BS_FLAG_NO_TMA):
+    for flags in (0, P.BS_FLAG_STAGED_FFT, P.BS_FLAG_NO_TMA):
         plan, off, ztr, zte = _run_beamspace(N, M, F, L, Ptr, Pte, W, K, u, P.BS_PREC_FP32, flags, xc)
         _check_windows(plan, off, ztr, zte, xc, M, L, Ptr, Pte, P.BS_PREC_FP32)
         outs.append((ztr, zte))
-    for a, b in zip(outs[0], outs[1]):
-        if a.size:
-            assert np.linalg.norm(a - b) <= 2 * FFT_TOL * np.linalg.norm(b)
+    for other in outs[1:]:
+        for a, b in zip(outs[0], other):
+            if a.size:
+                assert np.linalg.norm(a - b) <= 2 * FFT_TOL * np.linalg.norm(b)
+
+
+def test_warp_kernel_many_targets():
+    """256 targets (the most the warp-per-transform kernel stages per
+    vector) with W up to 16 at M = 1024 and M = 2048: gather entries beyond
+    the ones each lane keeps in registers, windows of every residue class."""
+    rng = np.random.default_rng(256)
+    T = 256
+    W = list(rng.integers(1, 17, size=T))
+    for N, M, F, L, Ptr, Pte in ((512, 1024, 64, 4, 2, 1), (1024, 2048, 32, 2, 2, 1)):
+        K = list(rng.integers(1, Ptr * (F // L) + 1, size=T))
+        Pn = Ptr + Pte
+        xc = (rng.standard_normal((Pn, F, N)) + 1j * rng.standard_normal((Pn, F, N))).astype(np.complex64)
+        u = list(rng.uniform(-0.99, 0.99, size=T))
+        for precision in (P.BS_PREC_FP32, P.BS_PREC_FP16):
+            ss = 2.0 if precision != P.BS_PREC_FP32 else 0.0
+            plan, off, ztr, zte = _run_beamspace(N, M, F, L, Ptr, Pte, W, K, u, precision, 0, xc, ss)
+            _check_windows(plan, off, ztr, zte, xc, M, L, Ptr, Pte, precision)
 
 
 def test_many_targets_gather_paths():
