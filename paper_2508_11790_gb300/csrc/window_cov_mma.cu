@@ -17,7 +17,10 @@
 // consumed; wider windows use 80-byte rows and 2 stages in the same 12 KB.
 // A window stream of one pair is latency-bound per warp: the bytes in flight
 // per SM set its bandwidth.  The accumulators are folded into double-float
-// every 128 vectors, and R is assembled in FP64.
+// every 128 vectors, and R is assembled in FP64.  The per-pair body is
+// compiled once per tile class ceil(2W / 8) = 1 .. 4, so tile counts, ring
+// stride and depth are constants and only the accumulators of tiles on or
+// below the diagonal exist; full 64-vector stages run an unrolled k loop.
 //
 // The covariance is HBM-bound (2 W flop per byte for 16-bit windows): the
 // tensor cores remove the FP32 multiply-add work that otherwise bounds the
@@ -75,24 +78,19 @@ __device__ __forceinline__ void df_fold(float &hi, float &lo, float b) {
 }
 
 
-template <int PREC>
-__global__ void __launch_bounds__(MMA_WARPS * 32)
-    window_cov_mma_kernel(const void *__restrict__ z, const int64_t *__restrict__ ztr_off,
-                          const int32_t *__restrict__ Wg, const int32_t *__restrict__ Kg,
-                          const int64_t *__restrict__ roff, const float *__restrict__ delta_pair, DF delta,
-                          DF inv_sc2, double2 *__restrict__ R, int64_t pairs) {
-    extern __shared__ __align__(16) uint16_t mma_smem[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t g = (int64_t)blockIdx.x * MMA_WARPS + warp;
-    if (g >= pairs) return;   // uniform per warp; no CTA-wide barrier below
-    uint16_t *ring = mma_smem + warp * MMA_WARP_HALVES;
-    const int W = Wg[g], K = Kg[g];
-    const int M2 = 2 * W;                       // real rows, <= 32
-    const int RS = (M2 <= 24) ? 24 : 40;        // stage row stride (16-bit elements)
-    const int nst = (M2 <= 24) ? 4 : 2;         // stages in the ring
+// One pair (the calling warp) of window size W with NNT = ceil(2W / 8)
+// 8-column tiles of A^T: the tile counts, the ring's row stride and depth
+// and the accumulators that exist are compile-time per class.
+template <int PREC, int NNT>
+__device__ __forceinline__ void cov_pair(uint16_t *ring, int lane, int64_t g, int W, int K, const void *z,
+                                         const int64_t *__restrict__ ztr_off, const int64_t *__restrict__ roff,
+                                         const float *__restrict__ delta_pair, DF delta, DF inv_sc2,
+                                         double2 *__restrict__ R) {
+    constexpr int nnt = NNT;                    // 8-column tiles of A^T
+    constexpr int nmt = (NNT + 1) / 2;          // 16-row tiles of A
+    constexpr int RS = (NNT <= 3) ? 24 : 40;    // stage row stride (16-bit elements): 2W <= 24 or <= 32
+    constexpr int nst = (NNT <= 3) ? 4 : 2;     // stages in the ring
     auto srow = [&](int b, int v) { return ring + (b * MMA_CH + v) * RS; };
-    const int nmt = (M2 + 15) >> 4;             // 16-row tiles of A
-    const int nnt = (M2 + 7) >> 3;              // 8-column tiles of A^T
     const uint32_t *zg = reinterpret_cast<const uint32_t *>(z) + ztr_off[g];   // one 32-bit word per complex
 
     // zero the ring (padding columns must read as 0)
@@ -135,7 +133,7 @@ __global__ void __launch_bounds__(MMA_WARPS * 32)
                 reinterpret_cast<uint32_t *>(srow(buf, n))[q] = 0u;
             __syncwarp();
         }
-        for (int kk = 0; kk < n; kk += 16) {
+        auto kstep = [&](int kk) {
             // A^T fragments (B operand) for column tiles 0..nnt-1, two tiles per ldmatrix.x4
             unsigned bfr[4][2];
 #pragma unroll
@@ -165,6 +163,12 @@ __global__ void __launch_bounds__(MMA_WARPS * 32)
                         if (nt < nnt && 16 * mt + 15 >= 8 * nt) mma16816<PREC>(acc[mt][nt], afr, bfr[nt][0], bfr[nt][1]);
                 }
             }
+        };
+        if (n == MMA_CH) {
+#pragma unroll
+            for (int kk = 0; kk < MMA_CH; kk += 16) kstep(kk);
+        } else {
+            for (int kk = 0; kk < n; kk += 16) kstep(kk);
         }
         // fold the FP32 accumulators (at most 128 vectors each) into double-float
         if (c % 2 == 1 || c == nch - 1) {
@@ -227,6 +231,29 @@ __global__ void __launch_bounds__(MMA_WARPS * 32)
             Rg[i * W + j] = make_double2(rd, id);
             Rg[j * W + i] = make_double2(rd, __longlong_as_double(__double_as_longlong(id) ^ (1ll << 63)));
         }
+    }
+}
+
+// One warp per pair; the pair's tile class is a warp-uniform switch (a
+// kernel compiled for one class alone was slower: with the shared memory
+// setting the occupancy, the smaller register budget only cost overlap).
+template <int PREC>
+__global__ void __launch_bounds__(MMA_WARPS * 32)
+    window_cov_mma_kernel(const void *__restrict__ z, const int64_t *__restrict__ ztr_off,
+                          const int32_t *__restrict__ Wg, const int32_t *__restrict__ Kg,
+                          const int64_t *__restrict__ roff, const float *__restrict__ delta_pair, DF delta,
+                          DF inv_sc2, double2 *__restrict__ R, int64_t pairs) {
+    extern __shared__ __align__(16) uint16_t mma_smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t g = (int64_t)blockIdx.x * MMA_WARPS + warp;
+    if (g >= pairs) return;   // uniform per warp; no CTA-wide barrier below
+    uint16_t *ring = mma_smem + warp * MMA_WARP_HALVES;
+    const int W = Wg[g], K = Kg[g];
+    switch ((2 * W + 7) >> 3) {   // warp-uniform
+        case 1: cov_pair<PREC, 1>(ring, lane, g, W, K, z, ztr_off, roff, delta_pair, delta, inv_sc2, R); break;
+        case 2: cov_pair<PREC, 2>(ring, lane, g, W, K, z, ztr_off, roff, delta_pair, delta, inv_sc2, R); break;
+        case 3: cov_pair<PREC, 3>(ring, lane, g, W, K, z, ztr_off, roff, delta_pair, delta, inv_sc2, R); break;
+        default: cov_pair<PREC, 4>(ring, lane, g, W, K, z, ztr_off, roff, delta_pair, delta, inv_sc2, R); break;
     }
 }
 
