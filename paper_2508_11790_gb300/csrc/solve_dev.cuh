@@ -250,6 +250,11 @@ static __device__ __noinline__ void solve_pair_fixed(unsigned mask, int lane, co
     constexpr int W = WT;
     const bool row = lane < W;
 
+    // Up to kKeepRow entries the lane's split row stays in registers for the
+    // refinement residual (else it is read and split again there).
+    constexpr int kKeepRow = 10;
+    constexpr int NK = (WT <= kKeepRow) ? WT : 1;
+    float4 Rrow[NK];
     float2 A[WT];
     bool finite = true;
 #pragma unroll
@@ -258,6 +263,7 @@ static __device__ __noinline__ void solve_pair_fixed(unsigned mask, int lane, co
         if (row) r = rows(j);
         finite = finite && isfinite(r.x) && isfinite(r.y);
         A[j] = make_float2(r.x, r.y);
+        if constexpr (WT <= kKeepRow) Rrow[j] = r;
     }
     const float2 ah = row ? a32g[lane] : make_float2(0.f, 0.f);
     const float2 al = row ? alog[lane] : make_float2(0.f, 0.f);
@@ -298,7 +304,9 @@ static __device__ __noinline__ void solve_pair_fixed(unsigned mask, int lane, co
         float2 v = chol_solve_f32<WT>(mask, lane, A, diag, Lsf, ah);
         // 3. refinement with a compensated (double-float) residual
         if (refine) {
-            const float2 r = residual_df<WT>(mask, lane, rows, ah, al, v);
+            float2 r;
+            if constexpr (WT <= kKeepRow) r = residual_df<WT>(mask, lane, [&](int j) { return Rrow[j]; }, ah, al, v);
+            else r = residual_df<WT>(mask, lane, rows, ah, al, v);
             const float2 dv = chol_solve_f32<WT>(mask, lane, A, diag, Lsf, r);
             v = cadd(v, dv);
         }
