@@ -22,15 +22,24 @@ pytestmark = pytest.mark.gpu
 FFT_TOL = 5e-6
 
 
-def _upa_config():
-    # window sizes W_z x W_x: 2 x 4 and 4 x 4 (the paper's), 2 x 2, 3 x 3, 1 x 5
-    return scaled_config(all_configs()["C1"], name="upa-4x32", N=128, Nz=4, M=512, Mz=8, T=5,
-                         W=(8, 16, 4, 9, 5), Wz=(2, 4, 2, 3, 1), K=64, P_tr=2, P_te=1, n_jam=2)
+def _upa_config(kind="paper"):
+    if kind == "paper":
+        # window sizes W_z x W_x: 2 x 4 and 4 x 4 (the paper's), 2 x 2, 3 x 3, 1 x 5
+        return scaled_config(all_configs()["C1"], name="upa-4x32", N=128, Nz=4, M=512, Mz=8, T=5,
+                             W=(8, 16, 4, 9, 5), Wz=(2, 4, 2, 3, 1), K=64, P_tr=2, P_te=1, n_jam=2)
+    if kind == "large":
+        # 4 x 128 elements, 8 x 256 beams: one vector per CTA (its buffers fill the shared memory)
+        return scaled_config(all_configs()["C1"], name="upa-4x128", N=512, Nz=4, M=2048, Mz=8, T=3,
+                             W=(16, 8, 6), Wz=(4, 2, 3), K=64, P_tr=2, P_te=1, n_jam=2)
+    # a single column (Nx = Mx = 1): no horizontal transform, windows 4 x 1 and 2 x 1
+    return scaled_config(all_configs()["C1"], name="upa-4x1", N=4, Nz=4, M=16, Mz=16, T=2,
+                         W=(4, 2), Wz=(4, 2), K=16, P_tr=1, P_te=1, n_jam=1)
 
 
-@pytest.mark.parametrize("precision", [P.BS_PREC_FP32, P.BS_PREC_FP16])
-def test_planar_pipeline_matches_oracle(precision):
-    cfg = _upa_config()
+@pytest.mark.parametrize("kind,precision", [("paper", P.BS_PREC_FP32), ("paper", P.BS_PREC_FP16),
+                                            ("large", P.BS_PREC_FP32), ("column", P.BS_PREC_FP32)])
+def test_planar_pipeline_matches_oracle(kind, precision):
+    cfg = _upa_config(kind)
     sc = make_scene(cfg)
     res = run_gpu(cfg, sc.x, sc.u_tgt, precision=precision, v=sc.v_tgt)
     ref = U.run_pipeline2d(sc.x, cfg, sc.u_tgt, sc.v_tgt)
@@ -58,7 +67,7 @@ def test_planar_pipeline_matches_oracle(precision):
         if precision == P.BS_PREC_FP32:
             assert e <= 1e-3, (g, e)
             assert rel(pr["out"], ref.out[k]) <= 2e-3, g
-    print(f"UPA precision {precision}: max weight rel err {worst_w:.2e}, max |SINR loss| {worst_loss:.2e} dB")
+    print(f"UPA {kind} precision {precision}: max weight rel err {worst_w:.2e}, max |SINR loss| {worst_loss:.2e} dB")
 
 
 def test_planar_rejects_linear_only_calls():
