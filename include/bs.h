@@ -339,8 +339,10 @@ bs_status bs_run(const bs_plan *plan, const bs_buffers *buf, bs_stream stream);
  * buf->x, runs the pass of bs_run, and copies buf->out back to out_host
  * ([pairs][Vte]). The copy is split into up to 8 record chunks issued on
  * a stream owned by the plan; channelisation and beamspace of chunk k run
- * on `stream` while chunk k+1 is copied, so the host link, not the
- * kernels, sets the time. Results are those of bs_run bit for bit.
+ * on `stream` while chunk k+1 is copied, and the covariance and solve run
+ * once the training records are done, while the test records are copied
+ * (the last chunk is one record), so the host link, not the kernels, sets
+ * the time. Results are those of bs_run bit for bit.
  * Synchronises `stream` before returning; one call per plan at a time. */
 bs_status bs_run_host(const bs_plan *plan, const bs_cf32 *x_host, bs_cf32 *out_host,
                       const bs_buffers *buf, bs_stream stream);

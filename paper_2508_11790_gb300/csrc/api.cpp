@@ -256,34 +256,49 @@ bs_status bs_run_host(const bs_plan *p, const bs_cf32 *x_host, bs_cf32 *out_host
     const size_t obytes = (size_t)p->pairs * p->Vte * sizeof(bs_cf32);
     // Record chunks: the copy of chunk k+1 (on the plan's copy stream) runs
     // while chunk k is channelised and transformed on `stream`; the host link
-    // is slower than the two stages, so only the last chunk's work and the
-    // covariance, solve and apply remain after the last copy.
-    const int P = p->P;
-    const int per = (P + bs_plan::kHostChunks - 1) / bs_plan::kHostChunks;
+    // is slower than the two stages.  Chunk boundaries fall at P_train, and
+    // the covariance and solve (training windows only) run as soon as the
+    // training chunks are transformed, under the copy of the test records;
+    // the last test chunk is one record, so that little work (its two
+    // stages, apply and the output copy) is left after the last copy.
+    const int P = p->P, Ptr = p->cfg.P_train, Pte = P - Ptr;
+    int bounds[bs_plan::kHostChunks + 1], nch = 0;
+    {
+        const int nte = Pte > 0 ? std::min(Pte, 3) : 0;
+        const int ntr = std::max(1, std::min(Ptr, bs_plan::kHostChunks - nte));
+        bounds[0] = 0;
+        for (int k = 1; k <= ntr; ++k) bounds[++nch] = (int)((int64_t)Ptr * k / ntr);
+        if (nte > 0) {   // nte - 1 even chunks, then one record
+            for (int k = 1; k < nte; ++k) bounds[++nch] = Ptr + (int)((int64_t)(Pte - 1) * k / (nte - 1));
+            bounds[++nch] = P;
+        }
+    }
     cudaError_t e = cudaEventRecord(p->ev_start, st);   // earlier work on `stream` is done with x
     if (e == cudaSuccess) e = cudaStreamWaitEvent(p->copy_st, p->ev_start, 0);
-    for (int k = 0, p0 = 0; p0 < P && e == cudaSuccess; ++k, p0 += per) {
-        const int np = std::min(per, P - p0);
+    for (int k = 0; k < nch && e == cudaSuccess; ++k) {
+        const int p0 = bounds[k], np = bounds[k + 1] - bounds[k];
         e = cudaMemcpyAsync((void *)(b->x + p0 * rec), x_host + p0 * rec, np * rec * sizeof(bs_cf32),
                             cudaMemcpyHostToDevice, p->copy_st);
         if (e == cudaSuccess) e = cudaEventRecord(p->ev_chunk[k], p->copy_st);
     }
     if (e != cudaSuccess) return bs::cuda_error(e, "host to device copy");
-    for (int k = 0, p0 = 0; p0 < P; ++k, p0 += per) {
-        const int np = std::min(per, P - p0);
+    bs_status s;
+    for (int k = 0; k < nch; ++k) {
+        const int p0 = bounds[k], np = bounds[k + 1] - bounds[k];
         e = cudaStreamWaitEvent(st, p->ev_chunk[k], 0);
         if (e != cudaSuccess) return bs::cuda_error(e, "stream wait");
-        if (bs_status s = bs::launch_channelize(p, (const float2 *)(b->x + p0 * rec), np, (float2 *)(b->xc + p0 * rec), st))
+        if ((s = bs::launch_channelize(p, (const float2 *)(b->x + p0 * rec), np, (float2 *)(b->xc + p0 * rec), st)))
             return s;
-        if (bs_status s = bs::launch_beamspace(p, (const float2 *)b->xc, b->z_train, (float2 *)b->z_test, st, p0, np))
+        if ((s = bs::launch_beamspace(p, (const float2 *)b->xc, b->z_train, (float2 *)b->z_test, st, p0, np)))
             return s;
-    }
-    bs_status s;
-    if (p->cfg.flags & BS_FLAG_FUSED) {
-        if ((s = bs_cov_solve(p, b->z_train, nullptr, b->R, b->c, b->info, stream))) return s;
-    } else {
-        if ((s = bs_window_cov(p, b->z_train, nullptr, b->R, stream))) return s;
-        if ((s = bs_mvdr_solve(p, b->R, b->c, b->info, stream))) return s;
+        if (bounds[k + 1] == Ptr) {   // every training window is in place
+            if (p->cfg.flags & BS_FLAG_FUSED) {
+                if ((s = bs_cov_solve(p, b->z_train, nullptr, b->R, b->c, b->info, stream))) return s;
+            } else {
+                if ((s = bs_window_cov(p, b->z_train, nullptr, b->R, stream))) return s;
+                if ((s = bs_mvdr_solve(p, b->R, b->c, b->info, stream))) return s;
+            }
+        }
     }
     if ((s = bs_apply(p, b->z_test, b->c, b->out, stream))) return s;
     if (obytes) {
