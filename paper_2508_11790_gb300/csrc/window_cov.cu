@@ -14,6 +14,7 @@
 namespace bs {
 
 constexpr int COV_THREADS = 128;
+constexpr int WMAX_COV = 16;             // largest window
 constexpr int COV_STAGE_ELEMS = 1024;  // window elements per staging buffer (8 KB in FP32)
 
 // (hi, lo) += b with Knuth's two-sum; the pair keeps ~48 bits.
@@ -179,6 +180,124 @@ __global__ void __launch_bounds__(COV_THREADS)
     }
 }
 
+// Short window streams (K <= 128): one warp per pair, four pairs per CTA.
+// The warp stages chunks of 64 vectors of its pair with coalesced loads;
+// lane l owns entries e = l + 32 k (k < ceil(E / 32) <= 5) of the lower
+// triangle (E = W (W + 1) / 2 <= 136, a per-pair switch on the count) and
+// sums z_i conj(z_j) over the vectors itself, in FP32 over
+// at most 16 vectors folded into double-float, so no reduction across
+// threads is needed; R is assembled as in window_cov_kernel.  With one CTA
+// per pair, a short stream left each thread at most a vector or two and
+// the CTA-wide reduction and barriers dominated.
+constexpr int COVW_WARPS = 4;
+constexpr int COVW_CH = 64;    // vectors per staged chunk
+
+// One pair (the calling warp) with EPL = ceil(W (W + 1) / 64) entries per
+// lane; lanes past the last entry accumulate entry (0, 0) and store nothing,
+// so the vector loop has no per-entry predicate.
+template <int PREC, int EPL>
+__device__ __forceinline__ void cov_warp_pair(unsigned char *sb, int lane, int64_t g, int W, int K,
+                                              const unsigned char *zg, const int64_t *__restrict__ roff,
+                                              const float *__restrict__ delta_pair, DF delta, float inv_sc,
+                                              double2 *__restrict__ R) {
+    constexpr int ES = (PREC == BS_PREC_FP32) ? 8 : 4;   // bytes per stored element
+    const int E = W * (W + 1) / 2;
+    int ii[EPL], jj[EPL];
+#pragma unroll
+    for (int k = 0; k < EPL; ++k) {
+        int i = 0, r = lane + 32 * k;
+        if (r < E) {
+            while (r > i) { r -= i + 1; ++i; }
+        } else {
+            r = 0;
+        }
+        ii[k] = i;
+        jj[k] = r;
+    }
+    float ar[EPL], ai[EPL], hr[EPL], lr[EPL], hi[EPL], li[EPL];
+#pragma unroll
+    for (int k = 0; k < EPL; ++k) ar[k] = ai[k] = hr[k] = lr[k] = hi[k] = li[k] = 0.f;
+    auto fold = [&]() {
+#pragma unroll
+        for (int k = 0; k < EPL; ++k) {
+            df_add(hr[k], lr[k], ar[k]);
+            df_add(hi[k], li[k], ai[k]);
+            ar[k] = ai[k] = 0.f;
+        }
+    };
+    int cnt = 0;
+    for (int k0 = 0; k0 < K; k0 += COVW_CH) {
+        const int n = min(COVW_CH, K - k0);
+        if constexpr (ES == 8) {
+            const float2 *src = reinterpret_cast<const float2 *>(zg) + (int64_t)k0 * W;
+            float2 *dst = reinterpret_cast<float2 *>(sb);
+            for (int q = lane; q < n * W; q += 32) dst[q] = __ldg(src + q);
+        } else {
+            const uint32_t *src = reinterpret_cast<const uint32_t *>(zg) + (int64_t)k0 * W;
+            uint32_t *dst = reinterpret_cast<uint32_t *>(sb);
+            for (int q = lane; q < n * W; q += 32) dst[q] = __ldg(src + q);
+        }
+        __syncwarp();
+        for (int v = 0, o = 0; v < n; ++v, o += W) {
+#pragma unroll
+            for (int k = 0; k < EPL; ++k) {   // z_i conj(z_j)
+                const float2 zi = widen<PREC>(sb, o + ii[k], inv_sc), zj = widen<PREC>(sb, o + jj[k], inv_sc);
+                ar[k] = fmaf(zi.x, zj.x, fmaf(zi.y, zj.y, ar[k]));
+                ai[k] = fmaf(zi.y, zj.x, fmaf(-zi.x, zj.y, ai[k]));
+            }
+            if (++cnt == 16) {
+                fold();
+                cnt = 0;
+            }
+        }
+        __syncwarp();   // the chunk is overwritten by the next one
+    }
+    fold();
+
+    // 1/K, the loading and R in double-float; FP64 only for the stored values
+    const float Kf = (float)K;
+    const float qk = 1.f / Kf;
+    const DF invK = df_norm(qk, fmaf(-qk, Kf, 1.f) / Kf);
+    const DF dl = delta_pair ? DF{delta_pair[g], 0.f} : delta;
+    double2 *Rg = R + roff[g];
+#pragma unroll
+    for (int k = 0; k < EPL; ++k) {
+        if (lane + 32 * k >= E) continue;
+        const int i = ii[k], j = jj[k];
+        const DF re = df_mul(df_norm(hr[k], lr[k]), invK);
+        if (i == j) {
+            Rg[i * W + i] = make_double2(df_to_double(df_add(re, dl)), 0.0);
+        } else {
+            const double rd = df_to_double(re), id = df_to_double(df_mul(df_norm(hi[k], li[k]), invK));
+            Rg[i * W + j] = make_double2(rd, id);
+            Rg[j * W + i] = make_double2(rd, __longlong_as_double(__double_as_longlong(id) ^ (1ll << 63)));
+        }
+    }
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(COVW_WARPS * 32)
+    window_cov_warp_kernel(const void *__restrict__ z, const int64_t *__restrict__ ztr_off,
+                           const int32_t *__restrict__ Wg, const int32_t *__restrict__ Kg,
+                           const int64_t *__restrict__ roff, const float *__restrict__ delta_pair, DF delta,
+                           float inv_sc, double2 *__restrict__ R, int64_t pairs) {
+    constexpr int ES = (PREC == BS_PREC_FP32) ? 8 : 4;   // bytes per stored element
+    __shared__ __align__(16) unsigned char stage[COVW_WARPS][COVW_CH * WMAX_COV * ES];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t g = (int64_t)blockIdx.x * COVW_WARPS + warp;
+    if (g >= pairs) return;   // uniform per warp; no CTA barrier below
+    const int W = Wg[g], K = Kg[g];
+    unsigned char *sb = stage[warp];
+    const unsigned char *zg = reinterpret_cast<const unsigned char *>(z) + ztr_off[g] * ES;
+    switch ((W * (W + 1) / 2 + 31) >> 5) {   // warp-uniform
+        case 1: cov_warp_pair<PREC, 1>(sb, lane, g, W, K, zg, roff, delta_pair, delta, inv_sc, R); break;
+        case 2: cov_warp_pair<PREC, 2>(sb, lane, g, W, K, zg, roff, delta_pair, delta, inv_sc, R); break;
+        case 3: cov_warp_pair<PREC, 3>(sb, lane, g, W, K, zg, roff, delta_pair, delta, inv_sc, R); break;
+        case 4: cov_warp_pair<PREC, 4>(sb, lane, g, W, K, zg, roff, delta_pair, delta, inv_sc, R); break;
+        default: cov_warp_pair<PREC, 5>(sb, lane, g, W, K, zg, roff, delta_pair, delta, inv_sc, R); break;
+    }
+}
+
 // Plain FP32 per-pair covariance: one CTA per pair, one thread per matrix
 // entry, one FP32 sum over all K vectors read straight from memory.
 __global__ void plain_cov_kernel(const float2 *__restrict__ z, const int64_t *__restrict__ ztr_off,
@@ -216,6 +335,26 @@ bs_status launch_window_cov(const bs_plan *p, const void *ztr, const float *delt
     if (p->cfg.precision != BS_PREC_FP32 && !(p->cfg.flags & BS_FLAG_SIMT_COV))
         return launch_window_cov_mma(p, ztr, delta, R, st);
     const float inv_sc = 1.0f / p->cfg.store_scale;
+    if (p->Kmax <= 128) {
+        if (p->Wmax > WMAX_COV) return set_error(BS_EUNSUPPORTED, "W > 16");
+        const unsigned blocks = (unsigned)((p->pairs + COVW_WARPS - 1) / COVW_WARPS);
+        const DF dl = df_from_double(p->cfg.delta);
+        switch (p->cfg.precision) {
+            case BS_PREC_FP32:
+                window_cov_warp_kernel<BS_PREC_FP32><<<blocks, COVW_WARPS * 32, 0, st>>>(
+                    ztr, p->d_ztr_off, p->d_Wg, p->d_Kg, p->d_roff, delta, dl, 1.0f, R, p->pairs);
+                break;
+            case BS_PREC_FP16:
+                window_cov_warp_kernel<BS_PREC_FP16><<<blocks, COVW_WARPS * 32, 0, st>>>(
+                    ztr, p->d_ztr_off, p->d_Wg, p->d_Kg, p->d_roff, delta, dl, inv_sc, R, p->pairs);
+                break;
+            default:
+                window_cov_warp_kernel<BS_PREC_BF16><<<blocks, COVW_WARPS * 32, 0, st>>>(
+                    ztr, p->d_ztr_off, p->d_Wg, p->d_Kg, p->d_roff, delta, dl, inv_sc, R, p->pairs);
+                break;
+        }
+        return check_launch("covariance (warp per pair) launch");
+    }
     switch (p->cfg.precision) {
         case BS_PREC_FP32:
             window_cov_kernel<BS_PREC_FP32><<<G, COV_THREADS, 0, st>>>(
