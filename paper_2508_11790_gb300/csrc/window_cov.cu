@@ -185,12 +185,19 @@ __global__ void __launch_bounds__(COV_THREADS)
 // lane l owns entries e = l + 32 k (k < ceil(E / 32) <= 5) of the lower
 // triangle (E = W (W + 1) / 2 <= 136, a per-pair switch on the count) and
 // sums z_i conj(z_j) over the vectors itself, in FP32 over
-// at most 16 vectors folded into double-float, so no reduction across
+// COVW_FOLD vectors folded into double-float, so no reduction across
 // threads is needed; R is assembled as in window_cov_kernel.  With one CTA
 // per pair, a short stream left each thread at most a vector or two and
 // the CTA-wide reduction and barriers dominated.
 constexpr int COVW_WARPS = 4;
 constexpr int COVW_CH = 64;    // vectors per staged chunk
+// FP32 partial sums cover COVW_FOLD vectors before they are folded into
+// double-float.  With 16 (the CTA kernel's bound) the worst MVDR weight
+// error of the short-stream workloads was 2.1e-4 (K = 18, W = 9) and 1.9e-3
+// (K = 6..120, W = 3..15); with 4 it is 5.7e-5 and 5.1e-4 (the CTA kernel,
+// which spreads a short stream over many thread slices so that its FP32
+// sums hold a product or two: 2.0e-5 and 1.1e-3).
+constexpr int COVW_FOLD = 4;
 
 // One pair (the calling warp) with EPL = ceil(W (W + 1) / 64) entries per
 // lane; lanes past the last entry accumulate entry (0, 0) and store nothing,
@@ -245,7 +252,7 @@ __device__ __forceinline__ void cov_warp_pair(unsigned char *sb, int lane, int64
                 ar[k] = fmaf(zi.x, zj.x, fmaf(zi.y, zj.y, ar[k]));
                 ai[k] = fmaf(zi.y, zj.x, fmaf(-zi.x, zj.y, ai[k]));
             }
-            if (++cnt == 16) {
+            if (++cnt == COVW_FOLD) {
                 fold();
                 cnt = 0;
             }
@@ -335,7 +342,7 @@ bs_status launch_window_cov(const bs_plan *p, const void *ztr, const float *delt
     if (p->cfg.precision != BS_PREC_FP32 && !(p->cfg.flags & BS_FLAG_SIMT_COV))
         return launch_window_cov_mma(p, ztr, delta, R, st);
     const float inv_sc = 1.0f / p->cfg.store_scale;
-    if (p->Kmax <= 128) {
+    if (p->Kmax <= 128 && p->pairs >= 4 * (int64_t)p->num_sms) {   // enough pairs to fill the GPU by warps
         if (p->Wmax > WMAX_COV) return set_error(BS_EUNSUPPORTED, "W > 16");
         const unsigned blocks = (unsigned)((p->pairs + COVW_WARPS - 1) / COVW_WARPS);
         const DF dl = df_from_double(p->cfg.delta);
