@@ -96,8 +96,8 @@ static __device__ __forceinline__ int solve_f64_rows(unsigned mask, int lane, in
         if (k < W) {
             const double dkk = __shfl_sync(mask, D[k].x, k, 16);
             if (!(dkk > 0.0) && fail == 0) fail = k + 1;
-            const double pk = sqrt(dkk > 0.0 ? dkk : 1.0);
-            const double inv = 1.0 / pk;
+            const double inv = rsqrt(dkk > 0.0 ? dkk : 1.0);   // one sequence instead of sqrt and a division
+            const double pk = (dkk > 0.0 ? dkk : 1.0) * inv;
             if (lane > k) D[k] = make_double2(D[k].x * inv, D[k].y * inv);
             if (lane == k) { D[k] = make_double2(pk, 0.0); diag = pk; }
 #pragma unroll
@@ -117,11 +117,14 @@ static __device__ __forceinline__ int solve_f64_rows(unsigned mask, int lane, in
     for (int j = 0; j < WMAX; ++j)
         if (row && j <= lane) Ld[lane][j] = D[j];
     __syncwarp(mask);
+    // one FP64 division per lane: GB300's FP64 pipe is narrow and a division
+    // is a long sequence on it (two per step of each solve before)
+    const double rdiag = 1.0 / diag;
     double2 acc = a, u = make_double2(0.0, 0.0);
 #pragma unroll
     for (int j = 0; j < WMAX; ++j) {
         if (j < W) {
-            const double2 mine = (lane == j) ? make_double2(acc.x / diag, acc.y / diag) : make_double2(0.0, 0.0);
+            const double2 mine = (lane == j) ? make_double2(acc.x * rdiag, acc.y * rdiag) : make_double2(0.0, 0.0);
             const double2 uj = shfl2d(mask, mine, j);
             if (lane == j) u = uj;
             if (lane > j) {
@@ -135,7 +138,7 @@ static __device__ __forceinline__ int solve_f64_rows(unsigned mask, int lane, in
 #pragma unroll
     for (int j = WMAX - 1; j >= 0; --j) {
         if (j < W) {
-            const double2 mine = (lane == j) ? make_double2(acc.x / diag, acc.y / diag) : make_double2(0.0, 0.0);
+            const double2 mine = (lane == j) ? make_double2(acc.x * rdiag, acc.y * rdiag) : make_double2(0.0, 0.0);
             const double2 vj = shfl2d(mask, mine, j);
             if (lane == j) v = vj;
             if (lane < j) {
@@ -147,9 +150,9 @@ static __device__ __forceinline__ int solve_f64_rows(unsigned mask, int lane, in
     // s = a^H v
     const double2 av = dconjmul(a, v);
     const double sr = hw_sum(mask, row ? av.x : 0.0), si = hw_sum(mask, row ? av.y : 0.0);
-    const double den = sr * sr + si * si;
+    const double rden = 1.0 / (sr * sr + si * si);
     // v / s = v conj(s) / |s|^2
-    c_out = make_double2((v.x * sr + v.y * si) / den, (v.y * sr - v.x * si) / den);
+    c_out = make_double2((v.x * sr + v.y * si) * rden, (v.y * sr - v.x * si) * rden);
     return 0;
 }
 
