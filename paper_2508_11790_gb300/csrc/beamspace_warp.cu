@@ -214,8 +214,7 @@ __device__ __forceinline__ void warp_units(const WarpArgs &wa, const GatherArgs 
 
         // entries in batches of kBatch: every shared-memory read of a batch
         // is issued before its stores (a dependent chain per entry otherwise);
-        // a missing entry (-1) reads target 0's row at a clamped beam and
-        // stores nothing
+        // a missing entry (-1) reads target 0's entry and stores nothing
         auto batch = [&](const int *pk) {
             float2 val[kBatch];
             long long gi[kBatch];
@@ -228,7 +227,9 @@ __device__ __forceinline__ void warp_units(const WarpArgs &wa, const GatherArgs 
                 ok[j] = packed >= 0 && w < te.n;
                 const int m = ((te.sw & 0xFFFF) + w) & (M - 1);
                 const int kk = m >> log2r;
-                val[j] = grp[(m & (R - 1)) * kBuf + (kk & 31) * kRow + (kk >> 5)];
+                // entries that store nothing (training vectors past the
+                // target's K) skip the shared-memory read
+                val[j] = ok[j] ? grp[(m & (R - 1)) * kBuf + (kk & 31) * kRow + (kk >> 5)] : make_float2(0.f, 0.f);
                 gi[j] = te.base + w;
             }
 #pragma unroll
