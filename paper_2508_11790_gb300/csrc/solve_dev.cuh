@@ -284,8 +284,8 @@ static __device__ __noinline__ void solve_pair_fixed(unsigned mask, int lane, co
     for (int k = 0; k < WT; ++k) {
         const float dkk = __shfl_sync(mask, A[k].x, k, 16);
         if (!(dkk > 0.f) && fail == 0) fail = k + 1;
-        const float pk = sqrtf(dkk > 0.f ? dkk : 1.f);
-        const float inv = 1.f / pk;
+        const float inv = rsqrtf(dkk > 0.f ? dkk : 1.f);   // the refinement step absorbs its last-bit error
+        const float pk = (dkk > 0.f ? dkk : 1.f) * inv;
         dmax = fmaxf(dmax, pk);
         dmin = fminf(dmin, pk);
         if (lane > k) A[k] = cscale(A[k], inv);
