@@ -23,3 +23,5 @@ from .beamspace_mvdr import __all__  # noqa: F401
 from . import learned_loading  # noqa: E402,F401
 from . import range_doppler  # noqa: E402,F401
 from . import upa  # noqa: E402,F401
+from .abi import (oracle_apply, oracle_beamspace, oracle_channelize, oracle_mvdr_solve,  # noqa: E402,F401
+                  oracle_pairs, oracle_window_cov)

@@ -358,3 +358,25 @@ def test_beam_pattern_grid_closed_forms():
     ch = O.lifted_correlator(O.mvdr_weights(R, at), N, M, beams)
     p0 = O.beam_pattern_grid(ch, [u0], f, fd)[0]
     assert p0 == pytest.approx(1.0 / (np.linalg.norm(ch) * np.sqrt(N)), rel=1e-12)
+
+
+def test_boundary_functions_compose_to_the_pipeline():
+    """The oracle_ functions of the five boundary calls, chained, give the
+    pipeline's windows, covariances, weights and outputs exactly."""
+    cfg = scaled_config(all_configs()["C1"], name="abi", T=3, W=(5, 3, 7), K=(40, 20, 64), L=8)
+    sc = make_scene(cfg)
+    ref = O.run_pipeline(sc.x, cfg, sc.u_tgt)
+    pairs = O.oracle_pairs(cfg, sc.u_tgt)
+    xc = O.oracle_channelize(sc.x, cfg.L)
+    assert xc.shape == sc.x.shape
+    ztr, zte = O.oracle_beamspace(xc, cfg, pairs)
+    R = O.oracle_window_cov(ztr, cfg.delta)
+    c = O.oracle_mvdr_solve(R, pairs.a_tilde)
+    out = O.oracle_apply(c, zte)
+    for g in range(len(pairs.t)):
+        assert int(pairs.t[g]) * cfg.L + int(pairs.s[g]) == g
+        np.testing.assert_array_equal(ztr[g], ref.z_train[g])
+        np.testing.assert_array_equal(zte[g], ref.z_test[g])
+        np.testing.assert_array_equal(R[g], ref.R[g])
+        np.testing.assert_array_equal(c[g], ref.c[g])
+        np.testing.assert_array_equal(out[g], ref.out[g])
