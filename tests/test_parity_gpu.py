@@ -438,6 +438,28 @@ def test_tensor_core_covariance(precision):
         np.testing.assert_allclose(pr["R"], pr["R"].conj().T, atol=0)
 
 
+@pytest.mark.parametrize("precision,flags", [(P.BS_PREC_FP32, 0), (P.BS_PREC_FP16, P.BS_FLAG_SIMT_COV)])
+def test_short_stream_covariance_warp_per_pair(precision, flags):
+    """Short window streams over many pairs (K <= 128, 1024 pairs) take the
+    warp-per-pair covariance: W = 1..16 (one to five lower-triangle entries
+    per lane), K = 1..128 across the 64-vector chunk boundary; R equals the
+    FP64 covariance of the same windows to COV_TOL."""
+    base = all_configs()["C1"]
+    W = (1, 2, 7, 8, 11, 13, 15, 16)
+    K = (1, 5, 63, 64, 65, 17, 128, 100)
+    cfg = scaled_config(base, name="warp-cov", N=64, F=512, L=128, M=64, T=len(W), W=W, K=K,
+                        P_te=1, n_jam=2)
+    sc = make_scene(cfg)
+    kw = {"store_scale": 4.0} if precision != P.BS_PREC_FP32 else {}
+    res = run_gpu(cfg, sc.x, sc.u_tgt, precision=precision, flags=flags, keep_xc=False, **kw)
+    assert res.plan.sizes.pairs == 1024
+    for g in range(res.plan.sizes.pairs):
+        pr = res.pair(g)
+        Ro = O.window_covariance(pr["z_train"].astype(np.complex128), cfg.delta)
+        assert np.abs(pr["R"] - Ro).max() <= COV_TOL * np.abs(Ro).max(), (g, np.abs(pr["R"] - Ro).max())
+        np.testing.assert_allclose(pr["R"], pr["R"].conj().T, atol=0)
+
+
 @pytest.mark.parametrize("precision", [P.BS_PREC_FP16, P.BS_PREC_BF16])
 def test_tensor_core_covariance_long_streams(precision):
     """K of several hundred vectors: the per-warp ring of window stages wraps
