@@ -145,7 +145,7 @@ struct WarpArgs {
 
 // One warp: residue CC of the beams of vectors vec, vec + vstride, ...
 // (kFull: N = 1024, no tail predicates).
-template <int R, bool kFull>
+template <int R, bool kFull, int PREC>
 __device__ __forceinline__ void warp_units(const WarpArgs &wa, const GatherArgs &ga, const float2 *tw,
                                            const float2 *ptw, float2 *grp, GatherEnt *tab,
                                            const int (&gent)[kWarpGatherRegs], int slot, int CC, int64_t vec,
@@ -168,12 +168,10 @@ __device__ __forceinline__ void warp_units(const WarpArgs &wa, const GatherArgs 
     auto put = [&](long long idx, float2 val, bool train) {
         if (!train) {
             ga.zte[idx] = cscale(val, wa.scale);
-        } else if (wa.prec == BS_PREC_FP16) {
-            store_train<BS_PREC_FP16>(ga.ztr, idx, val, wa.sc_tr);
-        } else if (wa.prec == BS_PREC_BF16) {
-            store_train<BS_PREC_BF16>(ga.ztr, idx, val, wa.sc_tr);
-        } else {
+        } else if constexpr (PREC == BS_PREC_FP32) {
             store_train<BS_PREC_FP32>(ga.ztr, idx, cscale(val, wa.sc_tr), 1.f);
+        } else {
+            store_train<PREC>(ga.ztr, idx, val, wa.sc_tr);
         }
     };
     if (vec < ga.nvec) load(vec);
@@ -251,7 +249,7 @@ __device__ __forceinline__ void warp_units(const WarpArgs &wa, const GatherArgs 
     }
 }
 
-template <int R, bool kFull>
+template <int R, bool kFull, int PREC>
 __global__ void __launch_bounds__(256, 2)
     beamspace_warp_kernel(WarpArgs wa, GatherArgs ga, const float2 *__restrict__ twM) {
     constexpr int M = 1024 * R, vpc = 8 / R;
@@ -278,10 +276,10 @@ __global__ void __launch_bounds__(256, 2)
     GatherEnt *tab = tabs + slot * ga.T;
     const int64_t vec = (int64_t)blockIdx.x * vpc + slot;
     const int64_t vstride = (int64_t)gridDim.x * vpc;
-    warp_units<R, kFull>(wa, ga, tw, ptw, grp, tab, gent, slot, cc, vec, vstride);
+    warp_units<R, kFull, PREC>(wa, ga, tw, ptw, grp, tab, gent, slot, cc, vec, vstride);
 }
 
-template <int R, bool kFull>
+template <int R, bool kFull, int PREC>
 bs_status launch_warp_t(const bs_plan *p, const float2 *xc, const GatherArgs &ga, cudaStream_t st) {
     constexpr int vpc = 8 / R;
     const size_t fixed = (size_t)R * 1056 * sizeof(float2) + 8 * (size_t)kBuf * sizeof(float2);
@@ -289,11 +287,11 @@ bs_status launch_warp_t(const bs_plan *p, const float2 *xc, const GatherArgs &ga
     const size_t smem_max = fixed + (size_t)vpc * kTabT * sizeof(GatherEnt);
     static int blocks_per_sm = 0;
     if (!blocks_per_sm) {
-        cudaError_t e = cudaFuncSetAttribute(beamspace_warp_kernel<R, kFull>,
+        cudaError_t e = cudaFuncSetAttribute(beamspace_warp_kernel<R, kFull, PREC>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
         if (e != cudaSuccess) return cuda_error(e, "beamspace (warp) attribute");
         int nb = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, beamspace_warp_kernel<R, kFull>, 256, smem_max);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, beamspace_warp_kernel<R, kFull, PREC>, 256, smem_max);
         if (e != cudaSuccess) return cuda_error(e, "beamspace (warp) occupancy");
         blocks_per_sm = std::max(nb, 1);
     }
@@ -308,8 +306,17 @@ bs_status launch_warp_t(const bs_plan *p, const float2 *xc, const GatherArgs &ga
     wa.sc_tr = (wa.prec == BS_PREC_FP32) ? wa.scale : wa.scale * ga.store_scale;
     wa.glist = p->d_glist;
     wa.sumW = p->sumW;
-    beamspace_warp_kernel<R, kFull><<<grid, 256, smem, st>>>(wa, ga, p->d_twM);
+    beamspace_warp_kernel<R, kFull, PREC><<<grid, 256, smem, st>>>(wa, ga, p->d_twM);
     return check_launch("beamspace (warp) launch");
+}
+
+template <int PREC>
+bs_status launch_warp_p(const bs_plan *p, const float2 *xc, const GatherArgs &ga, cudaStream_t st) {
+    const int M = p->cfg.M;
+    const bool full = p->cfg.N == 1024;
+    if (M == 1024) return full ? launch_warp_t<1, true, PREC>(p, xc, ga, st) : launch_warp_t<1, false, PREC>(p, xc, ga, st);
+    if (M == 2048) return full ? launch_warp_t<2, true, PREC>(p, xc, ga, st) : launch_warp_t<2, false, PREC>(p, xc, ga, st);
+    return full ? launch_warp_t<4, true, PREC>(p, xc, ga, st) : launch_warp_t<4, false, PREC>(p, xc, ga, st);
 }
 
 }  // namespace
@@ -322,10 +329,11 @@ bs_status launch_beamspace_warp(const bs_plan *p, const float2 *xc, const Gather
         (M != 1024 && M != 2048 && M != 4096))
         return BS_OK;
     *used = true;
-    const bool full = p->cfg.N == 1024;
-    if (M == 1024) return full ? launch_warp_t<1, true>(p, xc, ga, st) : launch_warp_t<1, false>(p, xc, ga, st);
-    if (M == 2048) return full ? launch_warp_t<2, true>(p, xc, ga, st) : launch_warp_t<2, false>(p, xc, ga, st);
-    return full ? launch_warp_t<4, true>(p, xc, ga, st) : launch_warp_t<4, false>(p, xc, ga, st);
+    switch (p->cfg.precision) {
+        case BS_PREC_FP32: return launch_warp_p<BS_PREC_FP32>(p, xc, ga, st);
+        case BS_PREC_FP16: return launch_warp_p<BS_PREC_FP16>(p, xc, ga, st);
+        default: return launch_warp_p<BS_PREC_BF16>(p, xc, ga, st);
+    }
 }
 
 }  // namespace bs
