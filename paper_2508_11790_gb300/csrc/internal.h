@@ -58,6 +58,10 @@ struct bs_plan {
     // fused covariance + solve: queue order (decreasing W^2 K), workspace head
     std::vector<int32_t> order;
     int32_t *d_order = nullptr;
+    // stand-alone solve: pairs grouped by W (stable), its visiting order
+    std::vector<int32_t> order_w;
+    int32_t *d_order_w = nullptr;
+    int Wmin = 0;
     int *d_head = nullptr;
     bs::CovSolveLaunch cs;
 };

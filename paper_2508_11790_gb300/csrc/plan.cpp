@@ -167,6 +167,7 @@ void bs_plan_destroy(bs_plan *p) {
     cudaFree(p->d_twM);
     cudaFree(p->d_err);
     cudaFree(p->d_order);
+    cudaFree(p->d_order_w);
     cudaFree(p->d_head);
     for (cudaEvent_t e : p->ev_chunk)
         if (e) cudaEventDestroy(e);
@@ -343,6 +344,14 @@ bs_status bs_plan_create(bs_plan **out, const bs_config *cfg) {
     std::stable_sort(p->order.begin(), p->order.end(), [&](int32_t x, int32_t y) {
         return (int64_t)p->Wg[x] * p->Wg[x] * p->Kg[x] > (int64_t)p->Wg[y] * p->Wg[y] * p->Kg[y];
     });
+    // the stand-alone solve visits pairs grouped by W, so that the CTAs
+    // resident together run the code of one window size (one solve body per
+    // W: mixed sizes side by side thrashed the instruction cache)
+    p->order_w.resize(G);
+    std::iota(p->order_w.begin(), p->order_w.end(), 0);
+    std::stable_sort(p->order_w.begin(), p->order_w.end(),
+                     [&](int32_t x, int32_t y) { return p->Wg[x] < p->Wg[y]; });
+    p->Wmin = *std::min_element(p->Wg.begin(), p->Wg.end());
 
     cudaGetDevice(&p->device);
     bs_status st = BS_OK;
@@ -365,6 +374,7 @@ bs_status bs_plan_create(bs_plan **out, const bs_config *cfg) {
     if (!st) st = upload(&p->d_twM, twiddles(c.M));
     if (!st) st = upload(&p->d_err, std::vector<int>(1, 0));
     if (!st) st = upload(&p->d_order, p->order);
+    if (!st) st = upload(&p->d_order_w, p->order_w);
     if (!st) st = upload(&p->d_head, std::vector<int>(1, 0));
     if (!st) st = bs::cuda_error(cudaStreamCreateWithFlags(&p->copy_st, cudaStreamNonBlocking), "copy stream");
     if (!st) st = bs::cuda_error(cudaEventCreateWithFlags(&p->ev_start, cudaEventDisableTiming), "event");
