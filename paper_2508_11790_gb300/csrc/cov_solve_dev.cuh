@@ -8,7 +8,8 @@
 //   1. forms the lower triangle of sum_k z_k z_k^H: its 16 lanes take
 //      (3x3 tile, k-slice) tasks; a task loads 6 window entries per vector
 //      (read-only path) and does 9 complex multiply-adds; FP32 sums cover
-//      at most 16 vectors and are folded into double-float (hi, lo);
+//      kCsFold = 4 vectors and are folded into double-float (hi, lo)
+//      (with 16 the worst C4 weight error was 1.9e-3);
 //   2. reduces the slices in double-float and forms R = sum / K + delta I in
 //      double-float, stored as FP64 in its shared memory (optionally also in
 //      global memory);
@@ -22,6 +23,8 @@
 #include "solve_dev.cuh"
 
 namespace bs {
+
+constexpr int kCsFold = 4;   // vectors per FP32 partial sum
 
 __device__ __forceinline__ void df_acc(float &hi, float &lo, float b) {
     const float s = hi + b;
@@ -123,7 +126,7 @@ __global__ void __launch_bounds__(NTH) cov_solve_kernel(CovSolveArgs a) {
                         ar[r][q] = fmaf(zi[r].x, zj[q].x, fmaf(zi[r].y, zj[q].y, ar[r][q]));
                         ai[r][q] = fmaf(zi[r].y, zj[q].x, fmaf(-zi[r].x, zj[q].y, ai[r][q]));
                     }
-                if (++cnt == 16) {
+                if (++cnt == kCsFold) {
 #pragma unroll
                     for (int r = 0; r < 3; ++r)
 #pragma unroll
