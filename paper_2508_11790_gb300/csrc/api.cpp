@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <string>
 
+#include "host_chunks.h"
 #include "internal.h"
 
 using bs::set_error;
@@ -261,18 +262,9 @@ bs_status bs_run_host(const bs_plan *p, const bs_cf32 *x_host, bs_cf32 *out_host
     // training chunks are transformed, under the copy of the test records;
     // the last test chunk is one record, so that little work (its two
     // stages, apply and the output copy) is left after the last copy.
-    const int P = p->P, Ptr = p->cfg.P_train, Pte = P - Ptr;
-    int bounds[bs_plan::kHostChunks + 1], nch = 0;
-    {
-        const int nte = Pte > 0 ? std::min(Pte, 3) : 0;
-        const int ntr = std::max(1, std::min(Ptr, bs_plan::kHostChunks - nte));
-        bounds[0] = 0;
-        for (int k = 1; k <= ntr; ++k) bounds[++nch] = (int)((int64_t)Ptr * k / ntr);
-        if (nte > 0) {   // nte - 1 even chunks, then one record
-            for (int k = 1; k < nte; ++k) bounds[++nch] = Ptr + (int)((int64_t)(Pte - 1) * k / (nte - 1));
-            bounds[++nch] = P;
-        }
-    }
+    const int Ptr = p->cfg.P_train;
+    int bounds[bs_plan::kHostChunks + 1];
+    const int nch = bs::host_chunk_bounds(Ptr, p->P - Ptr, bs_plan::kHostChunks, bounds);
     cudaError_t e = cudaEventRecord(p->ev_start, st);   // earlier work on `stream` is done with x
     if (e == cudaSuccess) e = cudaStreamWaitEvent(p->copy_st, p->ev_start, 0);
     for (int k = 0; k < nch && e == cudaSuccess; ++k) {
