@@ -23,6 +23,17 @@ def test_features_golden(golden):
     np.testing.assert_allclose(f, vals, atol=1e-15)
 
 
+def test_mlp_forward_golden(golden):
+    """Hand-worked forward pass of a 2-2-2-1 network (ReLU between layers)."""
+    rows = np.array([[float(v) for v in l.split()] for l in open(golden("mlp_2221.txt"))
+                     if l.strip() and not l.startswith("#")])
+    p = {"W1": np.array([[1.0, -1.0], [0.5, 2.0]]), "b1": np.array([0.0, -1.0]),
+         "W2": np.array([[1.0, 1.0], [-1.0, 0.5]]), "b2": np.array([0.5, 0.0]),
+         "W3": np.array([[2.0, -1.0]]), "b3": np.array([0.25])}
+    Y, _ = LL.mlp_forward(p, rows[:, :2])
+    np.testing.assert_allclose(Y[:, 0], rows[:, 2], atol=1e-15)
+
+
 def test_features_scale_invariance():
     W, K = 9, 18
     Z = crandn(K, W)

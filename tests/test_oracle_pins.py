@@ -274,6 +274,67 @@ def test_sinr_loss_of_mvdr_is_non_negative():
         assert O.sinr_loss_db(c + 0.01 * crandn(W), c, a, R) >= -1e-12
 
 
+def _read_output_golden(path):
+    outs, sinr = {}, None
+    with open(path) as fh:
+        for line in fh:
+            f = line.split()
+            if not f or f[0].startswith("#"):
+                continue
+            if f[0] == "out":
+                outs[int(f[1])] = float(f[2]) + 1j * float(f[3])
+            elif f[0] == "sinr":
+                sinr = float(f[1])
+    return outs, sinr
+
+
+def test_beamformer_output_and_sinr_golden(golden):
+    """Hand-worked c^H y (Sec. II-B) and |c^H a|^2 / (c^H R c) for W = 2."""
+    outs, sinr = _read_output_golden(golden("output_2x2.txt"))
+    c = np.array([1.0, 1j])
+    y = np.array([[1.0, 1.0], [1j, 0.0], [2.0, 3j]])
+    got = O.beamformer_output(c, y)
+    for k, v in outs.items():
+        assert got[k] == pytest.approx(v, abs=1e-15)
+    R = np.array([[2.0, 1j], [-1j, 2.0]])
+    assert O.output_sinr(c, np.array([1.0, 1.0]), R) == pytest.approx(sinr, abs=1e-15)
+
+
+@pytest.mark.parametrize("W", [1, 3, 9, 16])
+def test_beamformer_output_of_mvdr_is_distortionless(W):
+    """Eq. DefMVDR: the MVDR correlator passes its own steering vector with
+    unit gain, so the output for y = a~ is exactly 1 (a dropped conjugate or
+    a transposed product gives c^T a instead)."""
+    R = _rand_pd(W, 1e3)
+    a = crandn(W)
+    c = O.mvdr_weights(R, a)
+    out = O.beamformer_output(c, a[None, :])
+    assert out.shape == (1,)
+    assert out[0] == pytest.approx(1.0, abs=1e-10)
+    # linearity in the snapshots and anti-linearity in the weights
+    y = crandn(4, W)
+    np.testing.assert_allclose(O.beamformer_output(2j * c, y), -2j * O.beamformer_output(c, y), atol=1e-12)
+
+
+@pytest.mark.parametrize("W", [1, 4, 9])
+def test_output_sinr_of_mvdr_is_closed_form(W):
+    """Against its own covariance the MVDR output SINR is a^H R^-1 a
+    (distortionless gain 1 over output power 1/(a^H R^-1 a), Eq. CorrMVDR);
+    for R = s I + q b b^H, a^H R^-1 a follows from Sherman-Morrison in closed
+    form, independent of any solve."""
+    s, q = 2.5, 300.0
+    a, b = crandn(W), crandn(W)
+    R = s * np.eye(W) + q * np.outer(b, b.conj())
+    aa, ba, bb = np.vdot(a, a).real, np.vdot(b, a), np.vdot(b, b).real
+    closed = (aa - q * abs(ba) ** 2 / (s + q * bb)) / s
+    c = O.mvdr_weights(R, a)
+    assert O.output_sinr(c, a, R) == pytest.approx(closed, rel=1e-10)
+    # the conventional beamformer c = a: ||a||^4 / (s ||a||^2 + q |b^H a|^2)
+    assert O.output_sinr(a, a, R) == pytest.approx(aa ** 2 / (s * aa + q * abs(ba) ** 2), rel=1e-12)
+    # invariant to any complex scaling of the weights (|k|^2 over |k|^2)
+    assert O.output_sinr((0.3 - 2j) * c, a, R) == pytest.approx(closed, rel=1e-10)
+
+
 # --------------------------------------------------------------- whole path
 def test_pipeline_consistency_small():
     cfg = scaled_config(all_configs()["C1"], T=3, L=8, P_tr=2, P_te=2, K=40, W=(5, 3, 1))
