@@ -253,7 +253,8 @@ bs_status bs_set_launch(bs_plan *plan, int32_t threads, int32_t ctas_per_sm);
  * device buffers and forbids libraries to allocate).  Such callers cannot
  * create a bs_plan (plan creation allocates), so every per-pair table is
  * passed in, as device arrays of `pairs` entries:
- *   W, K        window size (1..16) and training-vector count (>= 1);
+ *   W, K        window size (1..16) and training-vector count
+ *               (1..2^24 - 1);
  *   ztr_off     element offset of the pair's K x W training windows in
  *               z_train (as bs_plan_offsets' ztr_off);
  *   woff        offset of the pair's W values in a_hi, a_lo, a_fp64 and c;
@@ -261,6 +262,8 @@ bs_status bs_set_launch(bs_plan *plan, int32_t threads, int32_t ctas_per_sm);
  *               (hi = (float)a, lo = (float)(a - hi)); a_fp64 the same in FP64.
  * Results are those of bs_cov_solve (R is not produced): c, info; a pair
  * whose W or K is out of range gets info = -3 and its c is not written.
+ * delta must be finite and >= 0 (BS_EINVAL otherwise); pairs == 0 is a
+ * no-op returning BS_OK.
  * This call allocates nothing: its scratch (queue head and cost-ordered pair
  * list) is a fixed array in device memory with room for 262144 pairs, held
  * by every GPU that loads the library until the process exits; larger

@@ -132,13 +132,13 @@ template <int M, bool kFull, int PREC>
 static bs_status launch_bs_t(const float2 *y, int64_t nvec, int N, const float2 *tw, float2 *out,
                              const GatherArgs &ga, cudaStream_t st) {
     using C = BsCfg<M>;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(beamspace_kernel<M, kFull, PREC>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem);
-        if (e != cudaSuccess) return cuda_error(e, "beamspace attribute");
-        attr_set = true;
-    }
+    static PerDevice attr;
+    if (bs_status s = attr.get([](int *) {
+            return cuda_error(cudaFuncSetAttribute(beamspace_kernel<M, kFull, PREC>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem),
+                              "beamspace attribute");
+        }))
+        return s;
     const int64_t blocks = (nvec + C::vpb - 1) / C::vpb;
     if (blocks > 0x7FFFFFFF) return set_error(BS_EUNSUPPORTED, "too many vectors");
     if (blocks == 0) return BS_OK;

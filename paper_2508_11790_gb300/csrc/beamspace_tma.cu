@@ -291,16 +291,22 @@ static bs_status launch_tma_t(const bs_plan *p, const float2 *y, const GatherArg
     using C = BsTmaCfg<M>;
     const size_t smem_max = 2 * C::work_bytes + 2 * (size_t)C::vpb * M * sizeof(float2) + 16;
     const size_t smem = 2 * C::work_bytes + 2 * (size_t)C::vpb * p->cfg.N * sizeof(float2) + 16;
-    static int blocks_per_sm = 0;
-    if (!blocks_per_sm) {
-        cudaError_t e = cudaFuncSetAttribute(beamspace_tma_kernel<M, kHalf>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
-        if (e != cudaSuccess) return cuda_error(e, "beamspace (TMA) attribute");
-        int nb = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, beamspace_tma_kernel<M, kHalf>, C::nthr, smem);
-        if (e != cudaSuccess) return cuda_error(e, "beamspace (TMA) occupancy");
-        blocks_per_sm = std::max(nb, 1);
-    }
+    static PerDevice occ;
+    int blocks_per_sm = 1;
+    if (bs_status s = occ.get(
+            [&](int *v) {
+                cudaError_t e = cudaFuncSetAttribute(beamspace_tma_kernel<M, kHalf>,
+                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
+                if (e != cudaSuccess) return cuda_error(e, "beamspace (TMA) attribute");
+                int nb = 0;
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, beamspace_tma_kernel<M, kHalf>, C::nthr,
+                                                                  smem_max);
+                if (e != cudaSuccess) return cuda_error(e, "beamspace (TMA) occupancy");
+                *v = std::max(nb, 1);
+                return BS_OK;
+            },
+            &blocks_per_sm))
+        return s;
     const int64_t ngroups = ga.nvec / C::vpb;
     if (ngroups == 0) return BS_OK;
     const int grid = (int)std::min<int64_t>(ngroups, (int64_t)p->num_sms * blocks_per_sm);

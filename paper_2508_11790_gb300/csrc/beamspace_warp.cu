@@ -285,16 +285,22 @@ bs_status launch_warp_t(const bs_plan *p, const float2 *xc, const GatherArgs &ga
     const size_t fixed = (size_t)R * 1056 * sizeof(float2) + 8 * (size_t)kBuf * sizeof(float2);
     const size_t smem = fixed + (size_t)vpc * ga.T * sizeof(GatherEnt);
     const size_t smem_max = fixed + (size_t)vpc * kTabT * sizeof(GatherEnt);
-    static int blocks_per_sm = 0;
-    if (!blocks_per_sm) {
-        cudaError_t e = cudaFuncSetAttribute(beamspace_warp_kernel<R, kFull, PREC>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
-        if (e != cudaSuccess) return cuda_error(e, "beamspace (warp) attribute");
-        int nb = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, beamspace_warp_kernel<R, kFull, PREC>, 256, smem_max);
-        if (e != cudaSuccess) return cuda_error(e, "beamspace (warp) occupancy");
-        blocks_per_sm = std::max(nb, 1);
-    }
+    static PerDevice occ;
+    int blocks_per_sm = 1;
+    if (bs_status s = occ.get(
+            [&](int *v) {
+                cudaError_t e = cudaFuncSetAttribute(beamspace_warp_kernel<R, kFull, PREC>,
+                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
+                if (e != cudaSuccess) return cuda_error(e, "beamspace (warp) attribute");
+                int nb = 0;
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, beamspace_warp_kernel<R, kFull, PREC>, 256,
+                                                                  smem_max);
+                if (e != cudaSuccess) return cuda_error(e, "beamspace (warp) occupancy");
+                *v = std::max(nb, 1);
+                return BS_OK;
+            },
+            &blocks_per_sm))
+        return s;
     const int64_t groups = (ga.nvec + vpc - 1) / vpc;
     if (groups == 0) return BS_OK;
     const int grid = (int)std::min<int64_t>(groups, (int64_t)p->num_sms * blocks_per_sm);

@@ -205,13 +205,13 @@ static bs_status launch_ch_tma(const bs_plan *pl, const float2 *x, int P, int N,
             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return BS_OK;   // fall back to the non-TMA kernel
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(channelize_tma_kernel<F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)C::smem);
-        if (e != cudaSuccess) return cuda_error(e, "channelize attribute");
-        attr_set = true;
-    }
+    static PerDevice attr;
+    if (bs_status s = attr.get([](int *) {
+            return cuda_error(cudaFuncSetAttribute(channelize_tma_kernel<F>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem),
+                              "channelize attribute");
+        }))
+        return s;
     const long long tiles = (long long)P * ((N + C::NT - 1) / C::NT);
     const int grid = (int)std::min<long long>(tiles, pl->num_sms);
     channelize_tma_kernel<F><<<grid, C::nthr, C::smem, st>>>(tmap, omap, N, P, pl->d_twF, 1.0f / sqrtf((float)F),
@@ -224,13 +224,13 @@ template <int F>
 static bs_status launch_ch(const float2 *x, int P, int N, float2 *xc, const float2 *tw,
                            cudaStream_t st) {
     using C = ChCfg<F>;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(channelize_kernel<F>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem);
-        if (e != cudaSuccess) return cuda_error(e, "channelize attribute");
-        attr_set = true;
-    }
+    static PerDevice attr;
+    if (bs_status s = attr.get([](int *) {
+            return cuda_error(cudaFuncSetAttribute(channelize_kernel<F>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem),
+                              "channelize attribute");
+        }))
+        return s;
     dim3 grid((N + C::NT - 1) / C::NT, P);
     channelize_kernel<F><<<grid, C::nthr, C::smem, st>>>(x, xc, N, tw, 1.0f / sqrtf((float)F));
     return check_launch("channelize launch");

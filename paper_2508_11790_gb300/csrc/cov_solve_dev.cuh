@@ -198,13 +198,13 @@ __global__ void __launch_bounds__(NTH) cov_solve_kernel(CovSolveArgs a) {
 template <int PREC, int NTH>
 bs_status launch_cs_t(const CovSolveArgs &a, int grid, cudaStream_t st) {
     constexpr size_t smem = (NTH / 16) * sizeof(HalfWarpSmem);
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(cov_solve_kernel<PREC, NTH>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return cuda_error(e, "cov_solve attribute");
-        attr_set = true;
-    }
+    static PerDevice attr;
+    if (bs_status s = attr.get([](int *) {
+            return cuda_error(cudaFuncSetAttribute(cov_solve_kernel<PREC, NTH>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                              "cov_solve attribute");
+        }))
+        return s;
     cov_solve_kernel<PREC, NTH><<<grid, NTH, smem, st>>>(a);
     return check_launch("cov_solve launch");
 }

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -71,6 +72,34 @@ namespace bs {
 bs_status set_error(bs_status s, const std::string &msg);
 bs_status cuda_error(cudaError_t e, const char *where);
 bs_status check_launch(const char *where);
+
+// Launch settings that a kernel needs once per device: function attributes
+// (the dynamic shared-memory limit) and occupancy apply to the current device
+// only, so a process that uses several GPUs sets them on each.  get() runs
+// init(&value) under a lock the first time the current device asks, caches
+// the value for that device, and returns it in *out (may be NULL).
+struct PerDevice {
+    static constexpr int kMaxDevices = 64;
+    std::mutex mu;
+    bool done[kMaxDevices] = {};
+    int val[kMaxDevices] = {};
+    template <class Init>
+    bs_status get(Init &&init, int *out = nullptr) {
+        int dev = 0;
+        const cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
+        if (dev < 0 || dev >= kMaxDevices) return set_error(BS_EUNSUPPORTED, "device index above 63");
+        std::lock_guard<std::mutex> lock(mu);
+        if (!done[dev]) {
+            int v = 0;
+            if (const bs_status s = init(&v)) return s;
+            val[dev] = v;
+            done[dev] = true;
+        }
+        if (out) *out = val[dev];
+        return BS_OK;
+    }
+};
 
 // kernel launchers (one per translation unit)
 bs_status launch_channelize(const bs_plan *p, const float2 *x, int P, float2 *xc, cudaStream_t st);

@@ -16,6 +16,7 @@
 // streams, or different host threads on one device) race on it and must not
 // be issued.  Each call rewrites the parts it uses (head and order list) in
 // its first kernel, so stale contents from an earlier call do no harm.
+#include <cmath>
 #include <mutex>
 
 #include "common.cuh"
@@ -29,7 +30,8 @@ constexpr int kNallocHdr = 64;                 // int32 slots before the order l
 static __device__ __align__(256) int32_t g_nalloc_scratch[kNallocHdr + kNallocMaxPairs];
 
 // Builds the queue in the scratch array: pairs whose table entry is out of
-// range (W outside 1..16 or K < 1) are placed first and skipped by setting
+// range (W outside 1..16, K outside 1..2^24 - 1; the covariance scale 1/K is
+// formed as a double-float that is exact only below 2^24) are placed first and skipped by setting
 // the head past them (info = -3); the others follow in decreasing order of
 // log2(W^2 K) (counting sort in shared memory, one CTA).
 __global__ void __launch_bounds__(1024)
@@ -42,10 +44,10 @@ __global__ void __launch_bounds__(1024)
     __syncthreads();
     auto bucket = [&](int64_t g) -> int {
         const int W = Wg[g], K = Kg[g];
-        if (W < 1 || W > 16 || K < 1) return 0;
-        const long long cost = (long long)W * W * K;
-        const int lg = 63 - __clzll(cost);   // 0 .. 36
-        return NB - 1 - lg;                  // 3 .. 39, larger cost first
+        if (W < 1 || W > 16 || K < 1 || K >= (1 << 24)) return 0;
+        const long long cost = (long long)W * W * K;   // < 2^32
+        const int lg = 63 - __clzll(cost);             // 0 .. 31
+        return NB - 1 - lg;                            // 8 .. 39, larger cost first
     };
     for (int64_t g = tid; g < pairs; g += blockDim.x) atomicAdd(&cnt[bucket(g)], 1);
     __syncthreads();
@@ -98,7 +100,7 @@ extern "C" bs_status bs_cov_solve_noalloc(const void *z_train, int32_t precision
     if (pairs > bs::kNallocMaxPairs)
         return set_error(BS_EINVAL, "bs_cov_solve_noalloc: pairs exceeds its fixed scratch of 262144 pairs");
     if (precision < BS_PREC_FP32 || precision > BS_PREC_BF16) return set_error(BS_EINVAL, "unknown precision");
-    if (!(delta >= 0.0)) return set_error(BS_EINVAL, "delta must be >= 0");
+    if (!(delta >= 0.0) || !std::isfinite(delta)) return set_error(BS_EINVAL, "delta must be finite and >= 0");
     if (pairs == 0) return BS_OK;
     if (!z_train || !W || !K || !ztr_off || !woff || !a_hi || !a_lo || !a_fp64 || !c || !info)
         return set_error(BS_EINVAL, "NULL buffer");

@@ -261,16 +261,16 @@ bs_status launch_window_cov_mma(const bs_plan *p, const void *ztr, const float *
                                 cudaStream_t st) {
     const int64_t G = p->pairs;
     const unsigned blocks = (unsigned)((G + MMA_WARPS - 1) / MMA_WARPS);
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(window_cov_mma_kernel<BS_PREC_FP16>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MMA_SMEM);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(window_cov_mma_kernel<BS_PREC_BF16>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MMA_SMEM);
-        if (e != cudaSuccess) return cuda_error(e, "covariance (tensor core) attribute");
-        attr_set = true;
-    }
+    static PerDevice attr;
+    if (bs_status s = attr.get([](int *) {
+            cudaError_t e = cudaFuncSetAttribute(window_cov_mma_kernel<BS_PREC_FP16>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MMA_SMEM);
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(window_cov_mma_kernel<BS_PREC_BF16>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MMA_SMEM);
+            return cuda_error(e, "covariance (tensor core) attribute");
+        }))
+        return s;
     const DF sc = df_from_double(1.0 / ((double)p->cfg.store_scale * (double)p->cfg.store_scale));
     const DF dl = df_from_double(p->cfg.delta);
     if (p->cfg.precision == BS_PREC_FP16)
