@@ -114,15 +114,30 @@ typedef struct {
     int32_t Mz;          /* vertical FFT size, power of 2, Nz <= Mz */
     const int32_t *Wz;   /* [T] host: vertical window size per target, dividing W[t] */
     const double  *v;    /* [T] host: vertical direction sine sin(theta) per target */
+    /* Subband shard (the subbands are processed independently once
+     * channelised, Sec. III-A): a plan with 0 < s_count < L covers only
+     * subbands s_begin .. s_begin + s_count - 1 of the L, so that G ranks can
+     * each run their own block.  s_count must be a power of two and s_begin
+     * a multiple of it.  Such a plan has pairs = T * s_count, pair
+     * g = t * s_count + (s - s_begin), and a channelised cube xc of
+     * [P][s_count * B][N] (the shard's bins of every record, in the order of
+     * the full cube); bs_channelize still reads whole raw records and writes
+     * only those bins.  Window starts and steering vectors use each
+     * subband's own centre frequency, so every pair's results equal those of
+     * the same pair of the unsharded plan.  bs_range_doppler needs every
+     * subband of a target and refuses a shard (BS_EUNSUPPORTED).
+     * s_count <= 0 or s_count == L: every subband (s_begin ignored). */
+    int32_t s_begin;
+    int32_t s_count;
 } bs_config;
 
 typedef struct {
-    int64_t pairs;        /* T * L */
+    int64_t pairs;        /* T * L (T * s_count for a subband shard) */
     int32_t B;            /* bins per subband, F / L */
     int32_t Vte;          /* test vectors per pair, P_test * B */
     int32_t W_max, K_max;
     int64_t x_elems;      /* cf32 elements of one raw cube, P*F*N, P = P_train+P_test */
-    int64_t xc_elems;     /* cf32 elements of the channelised cube, P*F*N */
+    int64_t xc_elems;     /* cf32 elements of the channelised cube, P*F*N (P*s_count*B*N for a shard) */
     int64_t ztrain_elems; /* complex elements of the training windows, sum W_g K_g */
     int64_t ztrain_bytes; /* bytes: 8 per element (FP32) or 4 (FP16/BF16) */
     int64_t ztest_elems;  /* cf32 elements of the test windows, sum W_g Vte */
@@ -169,9 +184,10 @@ bs_status bs_plan_offsets(const bs_plan *plan, int32_t *start, int32_t *W, int32
                           int64_t *roff, bs_cf64 *a_tilde);
 
 /* The same per-pair tables as bs_plan_create, computed on the host only (no
- * device is touched): start[T*L] window start beams and a_tilde[sum W_g]
- * windowed steering vectors (pair order, W_g values each).  Either output
- * may be NULL.  Errors: as bs_plan_create's argument checks. */
+ * device is touched): start[pairs] window start beams and a_tilde[sum W_g]
+ * windowed steering vectors (pair order, W_g values each; for a subband
+ * shard the shard's pairs).  Either output may be NULL.  Errors: as
+ * bs_plan_create's argument checks. */
 bs_status bs_plan_tables_host(const bs_config *cfg, int32_t *start, bs_cf64 *a_tilde);
 
 /* Synchronises the device and reads the plan's device error word, which a
@@ -180,11 +196,20 @@ bs_status bs_plan_tables_host(const bs_config *cfg, int32_t *start, bs_cf64 *a_t
  * Returns BS_ETIMEOUT if it was set, else BS_OK. */
 bs_status bs_plan_device_status(const bs_plan *plan, int32_t *flags);
 
+/* Writes the plan's device error word from the host (synchronous copy).
+ * flags = 0 clears it; a non-zero value makes the next
+ * bs_plan_device_status report BS_ETIMEOUT exactly as a kernel whose
+ * bounded wait gave up would, so that callers can test their handling of
+ * that error without a device wait running out. */
+bs_status bs_plan_set_device_flags(bs_plan *plan, int32_t flags);
+
 /* ----------------------------------------------------------- hot path --- */
 
 /* Channelise (Sec. III-A): for every record p < P and element n,
  *   xc[p][s*B + i][n] = F^-1/2 sum_t x[p][t][n] e^{-j 2 pi k t / F}
- * with k = ((s - L/2) B + i) mod F.  x, xc: [P][F][N] cf32, distinct. */
+ * with k = ((s - L/2) B + i) mod F.  x, xc: [P][F][N] cf32, distinct.  For
+ * a subband shard only s in s_begin .. s_begin + s_count - 1 is written,
+ * to xc[p][(s - s_begin) B + i][n] (xc: [P][s_count B][N]). */
 bs_status bs_channelize(const bs_plan *plan, const bs_cf32 *x, int32_t P,
                         bs_cf32 *xc, bs_stream stream);
 
@@ -208,22 +233,42 @@ bs_status bs_beamspace_full(const bs_plan *plan, const bs_cf32 *y, int64_t nvec,
 /* Loaded window covariance (Eq. EmpiricalCov on the windowed vectors, plus
  * loading): R_g = (1/K_g) sum_{v<K_g} z_v z_v^H + delta_g I, stored in FP64
  * (full Hermitian matrix).  delta_pair: NULL = plan delta, else a device
- * array [pairs] of per-pair loading (float).  FP32 windows: FP32 products,
- * partial sums of at most 16 vectors combined in double-float.  16-bit
- * windows: products on the tensor cores with FP32 accumulation, folded
- * into double-float every 128 vectors. */
+ * array [pairs] of per-pair loading (float).  FP32 windows: FP32 products;
+ * FP32 partial sums of at most 16 vectors (a CTA per pair) or of 4 vectors
+ * (a warp per pair, taken when K <= 128 and there are at least 4 pairs per
+ * SM) are combined in double-float (pairs of FP32, about 2^-47 relative).
+ * 16-bit windows: products on the tensor cores with FP32 accumulation,
+ * folded into double-float every 128 vectors. */
 bs_status bs_window_cov(const bs_plan *plan, const void *z_train, const float *delta_pair,
                         bs_cf64 *R, bs_stream stream);
 
 /* MVDR correlator (Eq. BeamCorrMVDR): c_g = R_g^-1 a~_g / (a~_g^H R_g^-1 a~_g).
  * FP32 Cholesky R = L L^H and two triangular solves, one refinement step
- * with the residual a~ - R v in FP64, normalisation in FP64.  Pairs whose
+ * whose residual a~ - R v is formed with error-free FP32 transformations
+ * from the double-float (hi + lo FP32) parts of R and a~ (about twice FP32
+ * precision; no FP64 arithmetic), then c = v / (a~^H v) in FP32.  Pairs whose
  * pivot ratio (max L_ii / min L_ii)^2 exceeds kappa_max, or whose FP32
  * factorisation fails, are solved again entirely in FP64.
  * info[g]: 0 = FP32 solve, -2 = solved in FP64, -1 = non-finite input,
  * k >= 1 = pivot k-1 not positive in FP64 (c_g set to NaN). */
 bs_status bs_mvdr_solve(const bs_plan *plan, const bs_cf64 *R, bs_cf32 *c, int32_t *info,
                         bs_stream stream);
+
+/* bs_mvdr_solve with a diagonal preconditioner (the seed the learned-loading
+ * network predicts, or any positive scaling): each d_i is rounded to the
+ * nearest power of two, 2^e_i (exponents clamped to [-30, 30]; non-positive
+ * or non-finite d_i count as 1), and with D = diag(2^e) the pair is solved
+ * as (D R D) y = D a~, c = D y / (a~^H D y) -- in exact arithmetic the c of
+ * bs_mvdr_solve (R^-1 a~ = D (D R D)^-1 D a~), and every scaling is exact,
+ * so only the conditioning the FP32 Cholesky sees (and with it the pivot
+ * ratio test for FP64 escalation) changes.  Jacobi scaling
+ * d_i = R_ii^-1/2 makes the diagonal of D R D lie in [1/2, 2].
+ * d: device [c_elems] FP32, packed like c (W_g values per pair).  Plans
+ * with BS_FLAG_PLAIN ignore d.  Results and info as bs_mvdr_solve.  The
+ * paper solves Eq. BeamCorrMVDR unscaled; the scaling follows the
+ * workload's learned preconditioner. */
+bs_status bs_mvdr_solve_precond(const bs_plan *plan, const bs_cf64 *R, const float *d, bs_cf32 *c, int32_t *info,
+                                bs_stream stream);
 
 /* Fused covariance + solve of every pair in one persistent launch (the
  * default of bs_run): the same results as bs_window_cov followed by
@@ -321,17 +366,26 @@ bs_status bs_beam_pattern(const bs_plan *plan, const bs_cf32 *c_hat, int32_t n_d
  * out: bs_apply's output [pairs][Vte]; pulse: [F] cf32 orthonormal spectrum
  * of the transmitted pulse (FFT order); work: caller-owned device scratch of
  * 2 T P_test F cf32; map: [T][P_test][F] FP32.  F is a power of two in
- * 16..4096 (plan validation). */
+ * 16..4096 (plan validation).  A subband-shard plan is refused
+ * (BS_EUNSUPPORTED): every subband of a target enters its map. */
 bs_status bs_range_doppler(const bs_plan *plan, const bs_cf32 *out, const bs_cf32 *pulse, bs_cf32 *work,
                            float *map, bs_stream stream);
 
-/* CFAR detection (Sec. IV: a threshold above the noise floor, 10 dB in the
- * paper): floor[t] = mean of map[t] over its P_test F cells (FP32 cells,
- * compensated sum); a cell is a detection when map > floor * 10^(dB/10),
- * compared in FP32.  floor: [T] FP32; count: [T] detections; mask (may be
- * NULL): [T][P_test][F] bytes, 1 for a detection. */
+/* CFAR detection (Sec. IV-B: a one-dimensional CFAR across all velocity
+ * bins of the range-Doppler map, 10 dB above the noise floor in the paper):
+ * the floor of cell (d, tau) of target t is the mean of the other
+ * P_test - 1 velocity bins of the same range cell,
+ *   floor[t][d][tau] = (sum_{d' != d} map[t][d'][tau]) / (P_test - 1)
+ * (FP32, summed in order of d'; the cell under test is left out), and the
+ * cell is a detection when map > floor * 10^(dB/10), compared in FP32.
+ * floor: [T][P_test][F] FP32; count: [T] detections; mask (may be NULL):
+ * [T][P_test][F] bytes, 1 for a detection; peak (may be NULL): [T] flat
+ * index d F + tau of the strongest detected cell (the smallest index on
+ * ties), -1 when the target has none -- its range and velocity bins, whose
+ * differences from the truth are the paper's detection errors.
+ * P_test == 0: no-op; P_test == 1: BS_EUNSUPPORTED. */
 bs_status bs_cfar(const bs_plan *plan, const float *map, float threshold_db, float *floor, int32_t *count,
-                  uint8_t *mask, bs_stream stream);
+                  uint8_t *mask, int32_t *peak, bs_stream stream);
 
 /* The whole pass on device buffers: channelise, beamspace, covariance,
  * solve (bs_cov_solve with BS_FLAG_FUSED), apply (delta = plan delta). */
@@ -433,6 +487,11 @@ bs_status bs_gather_rows(const float *src, const int64_t *idx, int64_t rows, int
  * result feeds bs_window_cov's per-pair loading. */
 bs_status bs_loading_from_mlp(const float *Y, int32_t nout, int64_t pairs, float lo, float hi, float fallback,
                               float *delta, bs_stream stream);
+
+/* The preconditioner seed: d[g][i] = 10^Y[g][1 + i], i < W (plans with one
+ * window size W; nout >= 1 + W), non-finite -> 1.  d: device [pairs][W],
+ * the packing of bs_mvdr_solve_precond's d for such plans. */
+bs_status bs_precond_from_mlp(const float *Y, int32_t nout, int64_t pairs, int32_t W, float *d, bs_stream stream);
 
 /* ------------------------------------------------------------- errors --- */
 const char *bs_status_string(bs_status s);

@@ -51,6 +51,7 @@ __all__ = [
     "output_sinr",
     "sinr_loss_db",
     "antenna_mvdr",
+    "reference_covariances",
     "PairTable",
     "pair_table",
     "PipelineResult",
@@ -324,3 +325,25 @@ def run_pipeline(x: np.ndarray, cfg, u, subbands=None, targets=None,
         zt.append(z_tr); ze.append(z_te); Rs.append(R); cs.append(c)
         outs.append(beamformer_output(c, z_te))
     return PipelineResult(tab, zt, ze, Rs, cs, outs)
+
+
+def reference_covariances(x_ref: np.ndarray, cfg, u, subbands=None, targets=None) -> list:
+    """Interference-plus-noise covariance of every selected pair, estimated
+    from target-free records x_ref[p, t, n] that the weights never saw:
+    R_ref = (1/K_ref) sum z z^H over all K_ref = P_ref B windowed vectors of
+    the pair (Eq. EmpiricalCov, no loading), in the order of pair_table.
+    Output SINR judged against R_ref measures how well a correlator
+    suppresses the scene's interference, not how well it fits its own
+    training sample."""
+    L, B, M = cfg.L, cfg.F // cfg.L, cfg.M
+    subs = list(range(L)) if subbands is None else [int(s) for s in subbands]
+    tab = pair_table(cfg, u, subs, targets)
+    yb = beamspace(channelize(x_ref, L, subs if subbands is not None else None), M)   # [P][S][B][M]
+    P = yb.shape[0]
+    out = []
+    for gi in range(len(tab.t)):
+        si = subs.index(int(tab.s[gi]))
+        beams = window_beams(int(tab.start[gi]), int(tab.W[gi]), M)
+        z = yb[:, si][:, :, beams].reshape(P * B, -1)
+        out.append(window_covariance(z, 0.0))
+    return out

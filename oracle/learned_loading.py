@@ -18,7 +18,11 @@ Definitions (restated in the design notes):
   d*_i = (R_ii + delta*)^(-1/2);
 * network: y = W3 relu(W2 relu(W1 x + b1) + b2) + b3 (3 layers);
 * loss: mean squared error over batch and outputs;
-* optimiser: Adam (Kingma and Ba, 2015), bias-corrected.
+* optimiser: Adam (Kingma and Ba, 2015), bias-corrected;
+* preconditioner: with D = diag(d), d > 0, the correlator is solved as
+  (D R D) y = D a, c = D y / (a^H D y) -- the same c as Eq. BeamCorrMVDR in
+  exact arithmetic (R^-1 a = D (D R D)^-1 D a), with a better-scaled
+  matrix for the finite-precision Cholesky when d equilibrates R.
 """
 from __future__ import annotations
 
@@ -36,6 +40,7 @@ __all__ = [
     "mlp_loss",
     "mlp_backward",
     "adam_step",
+    "mvdr_weights_preconditioned",
 ]
 
 # 61 log-spaced loading values from 1e-1 to 1e4 (noise variance units)
@@ -125,3 +130,16 @@ def adam_step(p: dict, g: dict, m: dict, v: dict, t: int, lr: float,
         mh = m[k] / (1 - beta1 ** t)
         vh = v[k] / (1 - beta2 ** t)
         p[k] = p[k] - lr * mh / (np.sqrt(vh) + eps)
+
+
+def mvdr_weights_preconditioned(R: np.ndarray, a: np.ndarray, d: np.ndarray) -> np.ndarray:
+    """MVDR correlator through the diagonally scaled system: solve
+    (D R D) y = D a with D = diag(d), then c = D y / (a^H D y)."""
+    R = np.asarray(R, np.complex128)
+    a = np.asarray(a, np.complex128)
+    d = np.asarray(d, np.float64)
+    if np.any(~(d > 0)):
+        raise ValueError("the preconditioner must be positive")
+    y = np.linalg.solve(d[:, None] * R * d[None, :], d * a)
+    v = d * y
+    return v / (np.conj(a) @ v)

@@ -14,14 +14,23 @@ above the noise floor (Sec. IV).  Readings taken here:
   rp[t][r][tau] = IFFT_k(Y[t][r][k] conj(P[k]))[tau];
 * Doppler is the unnormalised DFT over the test records:
   map[t][d][tau] = |sum_r rp[t][r][tau] e^{-j 2 pi d r / P_te}|^2;
-* CFAR: the noise floor of a target's map is its mean over all cells; a cell
-  is a detection when it exceeds the floor by the threshold (10 dB).
+* CFAR: a one-dimensional CFAR across the velocity bins of the map
+  (Sec. IV-B): the noise floor of cell (d, tau) is the mean of the other
+  P_te - 1 velocity bins of the same range cell tau (cell averaging with the
+  cell under test left out; with it included, a target alone in its range
+  cell could never clear 10 dB once P_te <= 10); a cell is a detection when
+  it exceeds its floor by the threshold (10 dB).  Needs P_te >= 2;
+* detection accuracy (Sec. IV-B: range and velocity error): a target's
+  detection is its strongest detected cell; its range error is the signed
+  difference of range bins and its velocity error the signed difference of
+  velocity bins taken modulo P_te into [-P_te/2, P_te/2); a target with no
+  detected cell is missed.
 """
 from __future__ import annotations
 
 import numpy as np
 
-__all__ = ["beamformed_spectrum", "range_profiles", "doppler_map", "cfar_detect"]
+__all__ = ["beamformed_spectrum", "range_profiles", "doppler_map", "cfar_detect", "detection_errors"]
 
 
 def beamformed_spectrum(out: np.ndarray, T: int, L: int, B: int, P_te: int) -> np.ndarray:
@@ -48,7 +57,31 @@ def doppler_map(rp: np.ndarray) -> np.ndarray:
 
 
 def cfar_detect(m: np.ndarray, threshold_db: float = 10.0):
-    """(mask, floor): cells of each target's map above its mean times
-    10^(threshold_db / 10)."""
-    floor = m.mean(axis=(1, 2))
-    return m > floor[:, None, None] * 10.0 ** (threshold_db / 10.0), floor
+    """(mask, floor), both [t][d][tau]: floor = mean of the other velocity
+    bins of the same range cell, mask = m > floor * 10^(threshold_db / 10)."""
+    m = np.asarray(m, np.float64)
+    Pd = m.shape[1]
+    if Pd < 2:
+        raise ValueError("a CFAR across velocity bins needs at least two bins")
+    floor = np.empty_like(m)
+    for d in range(Pd):
+        others = [e for e in range(Pd) if e != d]
+        floor[:, d, :] = m[:, others, :].sum(axis=1) / (Pd - 1)
+    return m > floor * 10.0 ** (threshold_db / 10.0), floor
+
+
+def detection_errors(mask: np.ndarray, m: np.ndarray, delay, doppler):
+    """Per target: (detected, peak cell (d, tau), range error, velocity
+    error).  The peak is the strongest detected cell (the first in
+    (d, tau) order on ties); errors are None for a missed target."""
+    T, Pd, _ = m.shape
+    out = []
+    for t in range(T):
+        if not mask[t].any():
+            out.append((False, None, None, None))
+            continue
+        masked = np.where(mask[t], m[t], -np.inf)
+        d, tau = np.unravel_index(int(np.argmax(masked)), masked.shape)
+        dv = (int(d) - int(doppler[t]) + Pd // 2) % Pd - Pd // 2
+        out.append((True, (int(d), int(tau)), int(tau) - int(delay[t]), dv))
+    return out

@@ -24,7 +24,7 @@ __all__ = [
     "bs_cov_solve", "bs_autotune", "bs_set_launch", "Graph", "bs_cov_solve_noalloc",
     "BsError", "Plan", "Buffers", "alloc_buffers", "lib", "bs_plan_tables_host",
     "bs_channelize", "bs_beamspace", "bs_beamspace_full", "bs_window_cov",
-    "bs_mvdr_solve", "bs_apply", "bs_run", "bs_run_host",
+    "bs_mvdr_solve", "bs_mvdr_solve_precond", "bs_apply", "bs_run", "bs_run_host",
     "bs_lift", "bs_apply_lifted", "bs_beam_pattern", "bs_range_doppler", "bs_cfar",
 ]
 
@@ -49,6 +49,7 @@ class _Config(ctypes.Structure):
         ("kappa_max", ctypes.c_double), ("store_scale", ctypes.c_float),
         ("Nz", ctypes.c_int32), ("Mz", ctypes.c_int32),
         ("Wz", ctypes.POINTER(ctypes.c_int32)), ("v", ctypes.POINTER(ctypes.c_double)),
+        ("s_begin", ctypes.c_int32), ("s_count", ctypes.c_int32),
     ]
 
 
@@ -86,11 +87,13 @@ _SIGS = {
     "bs_apply_lifted": ([_P, _P, _P, _P, _P], ctypes.c_int),
     "bs_beam_pattern": ([_P, _P, ctypes.c_int32, _P, _P, _P], ctypes.c_int),
     "bs_range_doppler": ([_P, _P, _P, _P, _P, _P], ctypes.c_int),
-    "bs_cfar": ([_P, _P, ctypes.c_float, _P, _P, _P, _P], ctypes.c_int),
+    "bs_cfar": ([_P, _P, ctypes.c_float, _P, _P, _P, _P, _P], ctypes.c_int),
     "bs_run": ([_P, ctypes.POINTER(_Buffers), _P], ctypes.c_int),
     "bs_run_host": ([_P, _P, _P, ctypes.POINTER(_Buffers), _P], ctypes.c_int),
     "bs_plan_tables_host": ([ctypes.POINTER(_Config), _P, _P], ctypes.c_int),
     "bs_plan_device_status": ([_P, _P], ctypes.c_int),
+    "bs_plan_set_device_flags": ([_P, ctypes.c_int32], ctypes.c_int),
+    "bs_mvdr_solve_precond": ([_P, _P, _P, _P, _P, _P], ctypes.c_int),
     "bs_cov_solve": ([_P, _P, _P, _P, _P, _P, _P], ctypes.c_int),
     "bs_autotune": ([_P, _P, _P, _P, _P, _P, _P, _P, _P], ctypes.c_int),
     "bs_set_launch": ([_P, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
@@ -168,9 +171,10 @@ class Sizes:
 
 
 def _make_config(N, F, L, M, u, W, K, P_train, P_test, fc, fs, fd, delta, precision=BS_PREC_FP32,
-                 flags=0, kappa_max=0.0, store_scale=0.0, Nz=1, Mz=1, Wz=None, v=None):
+                 flags=0, kappa_max=0.0, store_scale=0.0, Nz=1, Mz=1, Wz=None, v=None, s_begin=0, s_count=0):
     """ctypes config plus the numpy arrays it points into (keep both alive).
-    Nz > 1 (with Mz, per-target Wz and vertical sines v) makes it planar."""
+    Nz > 1 (with Mz, per-target Wz and vertical sines v) makes it planar;
+    0 < s_count < L restricts it to subbands s_begin .. s_begin + s_count - 1."""
     ua = np.ascontiguousarray(u, dtype=np.float64)
     Wa = np.ascontiguousarray(W, dtype=np.int32)
     Ka = np.ascontiguousarray(K, dtype=np.int32)
@@ -183,7 +187,8 @@ def _make_config(N, F, L, M, u, W, K, P_train, P_test, fc, fs, fd, delta, precis
                   Ka.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                   delta, precision, flags, kappa_max, store_scale, Nz, Mz,
                   Wza.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)) if planar else None,
-                  va.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if planar else None)
+                  va.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if planar else None,
+                  int(s_begin), int(s_count))
     return cfg, (ua, Wa, Ka, Wza, va)
 
 
@@ -191,9 +196,10 @@ def bs_plan_tables_host(**kw):
     """Window starts [T*L] and windowed steering vectors (packed, complex128)
     computed by the library on the host (no device needed)."""
     cfg, keep = _make_config(**kw)
-    G = cfg.T * cfg.L
+    Ls = cfg.s_count if 0 < cfg.s_count < cfg.L else cfg.L
+    G = cfg.T * Ls
     start = np.empty(G, np.int32)
-    at = np.empty(int(np.repeat(keep[1], cfg.L).sum()), np.complex128)
+    at = np.empty(int(np.repeat(keep[1], Ls).sum()), np.complex128)
     _check(lib().bs_plan_tables_host(ctypes.byref(cfg), start.ctypes.data, at.ctypes.data),
            "bs_plan_tables_host")
     return start, at
@@ -208,12 +214,15 @@ class Plan:
                  precision: int = BS_PREC_FP32, flags: int = 0,
                  kappa_max: float = 0.0, store_scale: float = 0.0,
                  Nz: int = 1, Mz: int = 1, Wz: Optional[Sequence[int]] = None,
-                 v: Optional[Sequence[float]] = None):
+                 v: Optional[Sequence[float]] = None, s_begin: int = 0, s_count: int = 0):
         self.T = len(u)
         cfg, self._keep = _make_config(N, F, L, M, u, W, K, P_train, P_test, fc, fs, fd, delta,
-                                       precision, flags, kappa_max, store_scale, Nz, Mz, Wz, v)
+                                       precision, flags, kappa_max, store_scale, Nz, Mz, Wz, v,
+                                       s_begin, s_count)
         self.Nz, self.Mz = Nz, Mz
         self.N, self.F, self.L, self.M = N, F, L, M
+        shard = 0 < s_count < L
+        self.s_begin, self.s_count = (int(s_begin), int(s_count)) if shard else (0, L)
         self.P_train, self.P_test = P_train, P_test
         self.precision, self.flags = precision, flags
         h = _P()
@@ -261,6 +270,10 @@ class Plan:
         st = lib().bs_plan_device_status(self._h, ctypes.byref(flags))
         _check(st, "bs_plan_device_status")
         return flags.value
+
+    def set_device_flags(self, flags: int) -> None:
+        """Write the device error word from the host (0 clears it)."""
+        _check(lib().bs_plan_set_device_flags(self._h, int(flags)), "bs_plan_set_device_flags")
 
     def close(self) -> None:
         if getattr(self, "_h", None):
@@ -355,6 +368,18 @@ def bs_mvdr_solve(plan: Plan, R: torch.Tensor, c: torch.Tensor, info: torch.Tens
            "bs_mvdr_solve")
 
 
+def bs_mvdr_solve_precond(plan: Plan, R: torch.Tensor, d: torch.Tensor, c: torch.Tensor, info: torch.Tensor,
+                          stream=None):
+    """bs_mvdr_solve with the diagonal preconditioner d (float32, packed
+    like c; each entry rounded to a power of two by the library)."""
+    s = plan.sizes
+    _check(lib().bs_mvdr_solve_precond(plan.handle, _ptr(R, torch.complex128, s.r_elems, "R"),
+                                       _ptr(d, torch.float32, s.c_elems, "d"),
+                                       _ptr(c, torch.complex64, s.c_elems, "c"),
+                                       _ptr(info, torch.int32, s.pairs, "info"), _stream(stream)),
+           "bs_mvdr_solve_precond")
+
+
 def bs_cov_solve(plan: Plan, z_train: torch.Tensor, c: torch.Tensor, info: torch.Tensor,
                  R: Optional[torch.Tensor] = None, delta_pair: Optional[torch.Tensor] = None, stream=None):
     s = plan.sizes
@@ -447,13 +472,16 @@ def bs_range_doppler(plan: Plan, out: torch.Tensor, pulse: torch.Tensor, work: t
 
 
 def bs_cfar(plan: Plan, rd_map: torch.Tensor, threshold_db: float, floor: torch.Tensor, count: torch.Tensor,
-            mask: Optional[torch.Tensor] = None, stream=None):
-    """CFAR over each target's map: floor [T] float32, count [T] int32,
-    optional mask [T * P_test * F] uint8."""
+            mask: Optional[torch.Tensor] = None, peak: Optional[torch.Tensor] = None, stream=None):
+    """CFAR across the velocity bins of each target's map: floor
+    [T * P_test * F] float32 (per cell), count [T] int32, optional mask
+    [T * P_test * F] uint8 and peak [T] int32 (strongest detected cell
+    d F + tau, -1 if none)."""
     n = plan.T * plan.P_test * plan.F
     _check(lib().bs_cfar(plan.handle, _ptr(rd_map, torch.float32, n, "map"), float(threshold_db),
-                         _ptr(floor, torch.float32, plan.T, "floor"), _ptr(count, torch.int32, plan.T, "count"),
-                         _ptr(mask, torch.uint8, n, "mask"), _stream(stream)), "bs_cfar")
+                         _ptr(floor, torch.float32, n, "floor"), _ptr(count, torch.int32, plan.T, "count"),
+                         _ptr(mask, torch.uint8, n, "mask"), _ptr(peak, torch.int32, plan.T, "peak"),
+                         _stream(stream)), "bs_cfar")
 
 
 def _cbuf(plan: Plan, b: Buffers) -> _Buffers:

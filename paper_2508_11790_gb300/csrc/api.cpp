@@ -67,6 +67,14 @@ bs_status bs_mvdr_solve(const bs_plan *p, const bs_cf64 *R, bs_cf32 *c, int32_t 
     return bs::launch_mvdr_solve(p, (const double2 *)R, (float2 *)c, info, (cudaStream_t)stream);
 }
 
+bs_status bs_mvdr_solve_precond(const bs_plan *p, const bs_cf64 *R, const float *d, bs_cf32 *c, int32_t *info,
+                                bs_stream stream) {
+    BS_REQUIRE(p, "NULL plan");
+    BS_REQUIRE(R && d && c && info, "NULL buffer");
+    if (bs_status s = check_device(p)) return s;
+    return bs::launch_mvdr_solve(p, (const double2 *)R, (float2 *)c, info, (cudaStream_t)stream, d);
+}
+
 bs_status bs_apply(const bs_plan *p, const bs_cf32 *z_test, const bs_cf32 *c, bs_cf32 *out, bs_stream stream) {
     BS_REQUIRE(p, "NULL plan");
     if (p->Vte == 0) return BS_OK;
@@ -108,6 +116,8 @@ bs_status bs_beam_pattern(const bs_plan *p, const bs_cf32 *c_hat, int32_t n_dirs
 bs_status bs_range_doppler(const bs_plan *p, const bs_cf32 *out, const bs_cf32 *pulse, bs_cf32 *work, float *map,
                            bs_stream stream) {
     BS_REQUIRE(p, "NULL plan");
+    if (p->Ls != p->cfg.L)
+        return set_error(BS_EUNSUPPORTED, "bs_range_doppler: a subband shard lacks the other subbands of each target");
     if (p->Vte == 0) return BS_OK;
     BS_REQUIRE(out && pulse && work && map, "NULL buffer");
     if (bs_status s = check_device(p)) return s;
@@ -116,12 +126,13 @@ bs_status bs_range_doppler(const bs_plan *p, const bs_cf32 *out, const bs_cf32 *
 }
 
 bs_status bs_cfar(const bs_plan *p, const float *map, float threshold_db, float *floor, int32_t *count,
-                  uint8_t *mask, bs_stream stream) {
+                  uint8_t *mask, int32_t *peak, bs_stream stream) {
     BS_REQUIRE(p, "NULL plan");
     if (p->Vte == 0) return BS_OK;
+    if (p->cfg.P_test < 2) return set_error(BS_EUNSUPPORTED, "bs_cfar: a CFAR across velocity bins needs P_test >= 2");
     BS_REQUIRE(map && floor && count, "NULL buffer");
     if (bs_status s = check_device(p)) return s;
-    return bs::launch_cfar(p, map, threshold_db, floor, count, mask, (cudaStream_t)stream);
+    return bs::launch_cfar(p, map, threshold_db, floor, count, mask, peak, (cudaStream_t)stream);
 }
 
 bs_status bs_cov_solve(const bs_plan *p, const void *z_train, const float *delta_pair, bs_cf64 *R, bs_cf32 *c,
@@ -253,7 +264,8 @@ bs_status bs_run_host(const bs_plan *p, const bs_cf32 *x_host, bs_cf32 *out_host
     BS_REQUIRE(b->z_test || p->cfg.P_test == 0, "z_test is NULL but P_test > 0");
     if (bs_status s = check_device(p)) return s;
     const cudaStream_t st = (cudaStream_t)stream;
-    const size_t rec = (size_t)p->cfg.F * p->cfg.N;   // elements per record
+    const size_t rec = (size_t)p->cfg.F * p->cfg.N;   // elements per raw record
+    const size_t crec = (size_t)p->Fs * p->cfg.N;     // elements per channelised record (the plan's bins)
     const size_t obytes = (size_t)p->pairs * p->Vte * sizeof(bs_cf32);
     // Record chunks: the copy of chunk k+1 (on the plan's copy stream) runs
     // while chunk k is channelised and transformed on `stream`; the host link
@@ -279,7 +291,7 @@ bs_status bs_run_host(const bs_plan *p, const bs_cf32 *x_host, bs_cf32 *out_host
         const int p0 = bounds[k], np = bounds[k + 1] - bounds[k];
         e = cudaStreamWaitEvent(st, p->ev_chunk[k], 0);
         if (e != cudaSuccess) return bs::cuda_error(e, "stream wait");
-        if ((s = bs::launch_channelize(p, (const float2 *)(b->x + p0 * rec), np, (float2 *)(b->xc + p0 * rec), st)))
+        if ((s = bs::launch_channelize(p, (const float2 *)(b->x + p0 * rec), np, (float2 *)(b->xc + p0 * crec), st)))
             return s;
         if ((s = bs::launch_beamspace(p, (const float2 *)b->xc, b->z_train, (float2 *)b->z_test, st, p0, np)))
             return s;

@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(BsCfg<M>::nthr, BsCfg<M>::minb)
         const int nv = (ga.nvec - vid0 < (int64_t)vpb) ? (int)(ga.nvec - vid0) : vpb;
         for (int e = tid; e < ga.ngather; e += nthr) {
             const int packed = __ldg(&ga.gather[e]);
-            const int t = packed >> 8, c = (packed >> 4) & 15, w = packed & 15;
+            const int t = packed >> 10, c = (packed >> 5) & 31, w = packed & 31;
             long long base;
             int sw, nout;
             if (t < kTabT) {
@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(BsCfg<M>::nthr, BsCfg<M>::minb)
         const int Fm1 = (1 << ga.log2F) - 1, Bm1 = (1 << ga.log2B) - 1;
         for (int e = tid; e < ga.ngather; e += nthr) {
             const int packed = __ldg(&ga.gather[e]);
-            const int t = packed >> 8, c = (packed >> 4) & 15, w = packed & 15;
+            const int t = packed >> 10, c = (packed >> 5) & 31, w = packed & 31;
             const int64_t g0 = (int64_t)t * ga.L;
             const int W = __ldg(&ga.Wg[g0]);
             const int64_t vid = vid0 + c;
@@ -174,12 +174,12 @@ bs_status launch_beamspace(const bs_plan *p, const float2 *xc, void *ztr, float2
                            int np) {
     if (np < 0) np = p->P - p0;
     GatherArgs ga;
-    ga.nvec = (int64_t)np * p->cfg.F;
-    ga.vbase = (int64_t)p0 * p->cfg.F;
+    ga.nvec = (int64_t)np * p->Fs;   // Fs = Ls B bins per record (F without a shard)
+    ga.vbase = (int64_t)p0 * p->Fs;
     xc += ga.vbase * p->cfg.N;   // the kernels index vectors of this range
-    ga.log2F = ilog2(p->cfg.F);
+    ga.log2F = ilog2(p->Fs);
     ga.log2B = ilog2(p->B);
-    ga.L = p->cfg.L;
+    ga.L = p->Ls;
     ga.T = p->cfg.T;
     ga.P_train = p->cfg.P_train;
     ga.uniform = (p->B % p->vpb) == 0;

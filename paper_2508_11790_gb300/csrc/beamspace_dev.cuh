@@ -25,7 +25,7 @@ struct GatherArgs {
     int64_t vbase;          // index of its first vector in the cube (multiple of F)
     int log2F, log2B, L, P_train, T;
     int uniform;            // B % vpb == 0: the vectors of a CTA share (record, subband)
-    const int32_t *gather;  // [vpb * sumW] (t << 8) | (c << 4) | w
+    const int32_t *gather;  // [vpb * sumW] (t << 10) | (c << 5) | w
     const longlong2 *gsub;  // [L][T][2]: {ztr_off, zte_off}, {start | W << 16, K}
     int ngather;
     const int32_t *Wg, *Kg, *start;

@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(256, 2)
     // entries tid + k * 256: its first kGatherRegs entries stay in registers
     // (re-reading the table for every group would go to L2: the L1 left
     // beside the shared memory of two CTAs does not keep it).  An entry
-    // (t, c, w) with t < kTabT is held decoded: t | k << 8 | c << 16 | w << 20
+    // (t, c, w) with t < kTabT is held decoded: t | k << 8 | c << 17 | w << 21
     // with k = c W_t + w its position in the target's run; others keep the
     // table's packing with bit 30 set; -1: no entry.
     int gent[kGatherRegs];
@@ -127,10 +127,10 @@ __global__ void __launch_bounds__(256, 2)
         int v = -1;
         if (e < ga.ngather) {
             const int packed = __ldg(&ga.gather[e]);
-            const int t = packed >> 8, c = (packed >> 4) & 15, w = packed & 15;
+            const int t = packed >> 10, c = (packed >> 5) & 31, w = packed & 31;
             if (t < kTabT) {
                 const int W = __ldg(&ga.Wg[(int64_t)t * ga.L]);
-                v = t | ((c * W + w) << 8) | (c << 16) | (w << 20);
+                v = t | ((c * W + w) << 8) | (c << 17) | (w << 21);
             } else {
                 v = packed | (1 << 30);
             }
@@ -252,8 +252,8 @@ __global__ void __launch_bounds__(256, 2)
                 store_train<BS_PREC_FP32>(ga.ztr, idx, cscale(val, sc_tr), 1.f);
             }
         };
-        auto gather_packed = [&](int packed) {   // table packing (t << 8) | (c << 4) | w
-            const int t = packed >> 8, c = (packed >> 4) & 15, w = packed & 15;
+        auto gather_packed = [&](int packed) {   // table packing (t << 10) | (c << 5) | w
+            const int t = packed >> 10, c = (packed >> 5) & 31, w = packed & 31;
             long long base;
             int sw, nout;
             if (t < kTabT) {
@@ -277,9 +277,9 @@ __global__ void __launch_bounds__(256, 2)
                 continue;
             }
             const GatherEnt te = tab[v & 255];
-            const int kk = (v >> 8) & 255;
+            const int kk = (v >> 8) & 511;
             if (kk >= te.n) continue;
-            const int c = (v >> 16) & 15, w = (v >> 20) & 15;
+            const int c = (v >> 17) & 15, w = (v >> 21) & 31;
             put(te.base + kk, X2[c * pl + padrow(((te.sw & 0xFFFF) + w) & (M - 1))]);
         }
         for (int e = tid + kGatherRegs * C::nthr; e < ga.ngather; e += C::nthr) gather_packed(__ldg(&ga.gather[e]));

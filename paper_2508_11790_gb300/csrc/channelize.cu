@@ -7,6 +7,9 @@
 // is produced by multiplying the input by (-1)^t (shift theorem), so no
 // extra permutation pass is needed.
 //
+// A subband shard writes only bins q0 .. q0 + Fs - 1 of each record, to rows
+// q - q0 of a cube of Fs rows per record (Fs = F without a shard).
+//
 // One CTA transforms NT consecutive elements (columns) of one record: the
 // first Stockham pass reads the columns straight from HBM (NT*8-byte
 // segments of each row), the middle passes run in padded shared memory and
@@ -36,16 +39,15 @@ struct ChCfg {
 template <int F>
 __global__ void __launch_bounds__(ChCfg<F>::nthr, ChCfg<F>::minb)
     channelize_kernel(const float2 *__restrict__ x, float2 *__restrict__ xc, int N,
-                      const float2 *__restrict__ tw, float scale) {
+                      const float2 *__restrict__ tw, float scale, int q0, int Fs) {
     using RP = Radix<F>;
     constexpr int NT = ChCfg<F>::NT;
     constexpr int nthr = ChCfg<F>::nthr;
     extern __shared__ float2 sm[];
     const int tid = threadIdx.x;
     const int n0 = blockIdx.x * NT;
-    const size_t rec = (size_t)blockIdx.y * F * N;
-    const float2 *xin = x + rec;
-    float2 *xout = xc + rec;
+    const float2 *xin = x + (size_t)blockIdx.y * F * N;
+    float2 *xout = xc + (size_t)blockIdx.y * Fs * N;
 
     auto gload = [&](int c, int t) -> float2 {
         const int n = n0 + c;
@@ -57,7 +59,7 @@ __global__ void __launch_bounds__(ChCfg<F>::nthr, ChCfg<F>::minb)
     auto sstore = [&](int c, int t, float2 v) { sm[padrow(t) * NT + c] = v; };
     auto gstore = [&](int c, int q, float2 v) {
         const int n = n0 + c;
-        if (n < N) xout[(size_t)q * N + n] = cscale(v, scale);
+        if (n < N && q >= q0 && q < q0 + Fs) xout[(size_t)(q - q0) * N + n] = cscale(v, scale);
     };
 
     if constexpr (RP::npass == 1) {
@@ -96,7 +98,8 @@ struct ChTmaCfg {
 template <int F>
 __global__ void __launch_bounds__(ChTmaCfg<F>::nthr, 1)
     channelize_tma_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap omap, int N,
-                          int P, const float2 *__restrict__ tw, float scale, int *__restrict__ err) {
+                          int P, const float2 *__restrict__ tw, float scale, int *__restrict__ err, int q0,
+                          int Fs, int obox) {
     using RP = Radix<F>;
     using C = ChTmaCfg<F>;
     constexpr int NT = C::NT;
@@ -161,10 +164,11 @@ __global__ void __launch_bounds__(ChTmaCfg<F>::nthr, 1)
         __syncthreads();
         stockham_pass<F, RP::r2, RP::r0 * RP::r1, NT, nthr, true, false>(tid, tw, sload, ostore);
         __syncthreads();   // output tile complete; work buffer consumed before the next tile's pass 0
-        if (tid == 0) {    // output tile to xc by TMA (columns beyond N are clipped)
+        if (tid == 0) {    // the shard's rows of the output tile to xc by TMA (columns beyond N clipped)
             fence_proxy_async();
 #pragma unroll 1
-            for (int r0 = 0; r0 < F; r0 += C::box_rows) tma_store_2d(&omap, ob + (size_t)r0 * NT, 2 * n0, p * F + r0);
+            for (int r0 = 0; r0 < Fs; r0 += obox)
+                tma_store_2d(&omap, ob + (size_t)(q0 + r0) * NT, 2 * n0, p * Fs + r0);
             bulk_commit();
         }
     }
@@ -194,14 +198,18 @@ static bs_status launch_ch_tma(const bs_plan *pl, const float2 *x, int P, int N,
     if (!enc) return BS_OK;
     if (reinterpret_cast<uintptr_t>(xc) & 15) return BS_OK;
     CUtensorMap tmap, omap;
+    const int Fs = pl->Fs, q0 = pl->s0 * pl->B;
+    const int obox = Fs < C::box_rows ? Fs : C::box_rows;   // q0 and Fs are multiples of obox
     const cuuint64_t gdim[2] = {(cuuint64_t)2 * N, (cuuint64_t)P * F};
+    const cuuint64_t odim[2] = {(cuuint64_t)2 * N, (cuuint64_t)P * Fs};
     const cuuint64_t gstride[1] = {(cuuint64_t)N * sizeof(float2)};
     const cuuint32_t box[2] = {(cuuint32_t)(2 * C::NT), (cuuint32_t)C::box_rows};
+    const cuuint32_t obx[2] = {(cuuint32_t)(2 * C::NT), (cuuint32_t)obox};
     const cuuint32_t estr[2] = {1, 1};
     if (enc(&tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float2 *>(x), gdim, gstride, box, estr,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS ||
-        enc(&omap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, xc, gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+        enc(&omap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, xc, odim, gstride, obx, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return BS_OK;   // fall back to the non-TMA kernel
@@ -215,13 +223,13 @@ static bs_status launch_ch_tma(const bs_plan *pl, const float2 *x, int P, int N,
     const long long tiles = (long long)P * ((N + C::NT - 1) / C::NT);
     const int grid = (int)std::min<long long>(tiles, pl->num_sms);
     channelize_tma_kernel<F><<<grid, C::nthr, C::smem, st>>>(tmap, omap, N, P, pl->d_twF, 1.0f / sqrtf((float)F),
-                                                            pl->d_err);
+                                                            pl->d_err, q0, Fs, obox);
     *used = true;
     return check_launch("channelize (TMA) launch");
 }
 
 template <int F>
-static bs_status launch_ch(const float2 *x, int P, int N, float2 *xc, const float2 *tw,
+static bs_status launch_ch(const float2 *x, int P, int N, float2 *xc, const float2 *tw, int q0, int Fs,
                            cudaStream_t st) {
     using C = ChCfg<F>;
     static PerDevice attr;
@@ -232,12 +240,13 @@ static bs_status launch_ch(const float2 *x, int P, int N, float2 *xc, const floa
         }))
         return s;
     dim3 grid((N + C::NT - 1) / C::NT, P);
-    channelize_kernel<F><<<grid, C::nthr, C::smem, st>>>(x, xc, N, tw, 1.0f / sqrtf((float)F));
+    channelize_kernel<F><<<grid, C::nthr, C::smem, st>>>(x, xc, N, tw, 1.0f / sqrtf((float)F), q0, Fs);
     return check_launch("channelize launch");
 }
 
 bs_status launch_channelize(const bs_plan *p, const float2 *x, int P, float2 *xc, cudaStream_t st) {
     const int N = p->cfg.N;
+    const int q0 = p->s0 * p->B, Fs = p->Fs;
     if (!(p->cfg.flags & BS_FLAG_NO_TMA)) {
         bool used = false;
         bs_status s = BS_OK;
@@ -250,15 +259,15 @@ bs_status launch_channelize(const bs_plan *p, const float2 *x, int P, float2 *xc
         if (s || used) return s;
     }
     switch (p->cfg.F) {
-        case 16: return launch_ch<16>(x, P, N, xc, p->d_twF, st);
-        case 32: return launch_ch<32>(x, P, N, xc, p->d_twF, st);
-        case 64: return launch_ch<64>(x, P, N, xc, p->d_twF, st);
-        case 128: return launch_ch<128>(x, P, N, xc, p->d_twF, st);
-        case 256: return launch_ch<256>(x, P, N, xc, p->d_twF, st);
-        case 512: return launch_ch<512>(x, P, N, xc, p->d_twF, st);
-        case 1024: return launch_ch<1024>(x, P, N, xc, p->d_twF, st);
-        case 2048: return launch_ch<2048>(x, P, N, xc, p->d_twF, st);
-        case 4096: return launch_ch<4096>(x, P, N, xc, p->d_twF, st);
+        case 16: return launch_ch<16>(x, P, N, xc, p->d_twF, q0, Fs, st);
+        case 32: return launch_ch<32>(x, P, N, xc, p->d_twF, q0, Fs, st);
+        case 64: return launch_ch<64>(x, P, N, xc, p->d_twF, q0, Fs, st);
+        case 128: return launch_ch<128>(x, P, N, xc, p->d_twF, q0, Fs, st);
+        case 256: return launch_ch<256>(x, P, N, xc, p->d_twF, q0, Fs, st);
+        case 512: return launch_ch<512>(x, P, N, xc, p->d_twF, q0, Fs, st);
+        case 1024: return launch_ch<1024>(x, P, N, xc, p->d_twF, q0, Fs, st);
+        case 2048: return launch_ch<2048>(x, P, N, xc, p->d_twF, q0, Fs, st);
+        case 4096: return launch_ch<4096>(x, P, N, xc, p->d_twF, q0, Fs, st);
     }
     return set_error(BS_EUNSUPPORTED, "F not supported");
 }

@@ -21,6 +21,9 @@ struct CovSolveLaunch {
 struct bs_plan {
     bs_config cfg;              // host pointers cleared after create
     int B = 0, P = 0, Vte = 0, Wmax = 0, Kmax = 0, sumW = 0;
+    // subbands of the plan: s0 .. s0 + Ls - 1 of the cfg.L (a shard, or all);
+    // Fs = Ls B bins per record in the channelised cube
+    int s0 = 0, Ls = 0, Fs = 0;
     int64_t pairs = 0;
     std::vector<int32_t> Wt, Kt;        // per target
     std::vector<double> u;              // per target
@@ -36,7 +39,7 @@ struct bs_plan {
     int64_t ztr_elems = 0, zte_elems = 0, r_elems = 0, c_elems = 0;
     // beamspace gather: vectors per CTA and the (target, k) table of one CTA
     int vpb = 0;
-    std::vector<int32_t> gather;        // [vpb * sumW]: (t << 8) | (c << 4) | w, target-major
+    std::vector<int32_t> gather;        // [vpb * sumW]: (t << 10) | (c << 5) | w, target-major
     std::vector<int32_t> glist;         // [sumW]: (t << 8) | w, target-major (one vector)
     // per (subband, target), subband-major: {ztr_off, zte_off, start | W << 16, K}
     std::vector<int64_t> gsub;
@@ -112,8 +115,9 @@ bs_status launch_window_cov(const bs_plan *p, const void *ztr, const float *delt
                             cudaStream_t st);
 bs_status launch_window_cov_mma(const bs_plan *p, const void *ztr, const float *delta, double2 *R,
                                 cudaStream_t st);
+// dpre: optional diagonal preconditioner [c_elems] (woff-packed), NULL for none
 bs_status launch_mvdr_solve(const bs_plan *p, const double2 *R, float2 *c, int32_t *info,
-                            cudaStream_t st);
+                            cudaStream_t st, const float *dpre = nullptr);
 bs_status launch_apply(const bs_plan *p, const float2 *zte, const float2 *c, float2 *out,
                        cudaStream_t st);
 bs_status launch_cov_solve(const bs_plan *p, const void *ztr, const float *delta, double2 *R, float2 *c,
@@ -131,7 +135,7 @@ bs_status launch_fft_rows(const bs_plan *p, const float2 *y, int64_t nvec, float
 bs_status launch_range_doppler(const bs_plan *p, const float2 *out, const float2 *pulse, float2 *work, float *map,
                                cudaStream_t st);
 bs_status launch_cfar(const bs_plan *p, const float *map, float threshold_db, float *floor, int32_t *count,
-                      uint8_t *mask, cudaStream_t st);
+                      uint8_t *mask, int32_t *peak, cudaStream_t st);
 bs_status launch_apply_lifted(const bs_plan *p, const float2 *xc, const float2 *c_hat, float2 *out,
                               cudaStream_t st);
 bs_status launch_beam_pattern(const bs_plan *p, const float2 *c_hat, int n_dirs, const double *u, float *pattern,

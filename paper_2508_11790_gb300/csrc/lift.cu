@@ -103,12 +103,12 @@ __global__ void __launch_bounds__(256)
 // one CTA per pair, a warp per direction
 __global__ void __launch_bounds__(256)
     beam_pattern_kernel(const float2 *__restrict__ c_hat, const double *__restrict__ u, int n_dirs, int N, int L,
-                        double fc, double fs, double fd, float *__restrict__ pattern) {
+                        int Ls, int s0, double fc, double fs, double fd, float *__restrict__ pattern) {
     extern __shared__ float2 ch[];   // [N] c_hat, then [n_dirs] Omega / pi as FP32 (hi, lo)
     float2 *omt = ch + N;
     __shared__ float part[8];
     const int64_t g = blockIdx.x;
-    const int s = (int)(g % L);
+    const int s = s0 + (int)(g % Ls);   // subband of pair g among the L (plans of a shard: s0 + local)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float nrm = 0.f;
     for (int n = threadIdx.x; n < N; n += 256) {
@@ -188,11 +188,11 @@ bs_status launch_lift(const bs_plan *p, const float2 *c, float2 *c_hat, cudaStre
 
 bs_status launch_apply_lifted(const bs_plan *p, const float2 *xc, const float2 *c_hat, float2 *out,
                               cudaStream_t st) {
-    const int T = p->cfg.T, L = p->cfg.L, Vte = p->Vte;
+    const int T = p->cfg.T, L = p->Ls, Vte = p->Vte;   // the plan's subbands, Fs bins per record of xc
     if (Vte == 0 || p->pairs == 0) return BS_OK;
     if (L > 65535) return set_error(BS_EUNSUPPORTED, "apply_lifted: at most 65535 subbands");
     dim3 grid((T + AL_T - 1) / AL_T, (Vte + AL_V - 1) / AL_V, L);
-    apply_lifted_kernel<<<grid, 256, 0, st>>>(xc, c_hat, out, p->cfg.N, p->cfg.F, p->B, L, T, p->cfg.P_train, Vte);
+    apply_lifted_kernel<<<grid, 256, 0, st>>>(xc, c_hat, out, p->cfg.N, p->Fs, p->B, L, T, p->cfg.P_train, Vte);
     return check_launch("apply_lifted launch");
 }
 
@@ -206,8 +206,8 @@ bs_status launch_beam_pattern(const bs_plan *p, const float2 *c_hat, int n_dirs,
                                              (int)smem);
         if (e != cudaSuccess) return cuda_error(e, "beam pattern attribute");
     }
-    beam_pattern_kernel<<<(unsigned)p->pairs, 256, smem, st>>>(c_hat, u, n_dirs, p->cfg.N, p->cfg.L, p->cfg.fc,
-                                                              p->cfg.fs, p->cfg.fd, pattern);
+    beam_pattern_kernel<<<(unsigned)p->pairs, 256, smem, st>>>(c_hat, u, n_dirs, p->cfg.N, p->cfg.L, p->Ls, p->s0,
+                                                              p->cfg.fc, p->cfg.fs, p->cfg.fd, pattern);
     return check_launch("beam pattern launch");
 }
 

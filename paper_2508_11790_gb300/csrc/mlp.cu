@@ -239,6 +239,19 @@ __global__ void loading_from_mlp_kernel(const float *__restrict__ Y, int nout, i
     delta[g] = fminf(fmaxf(d, lo), hi);
 }
 
+// d[g][i] = 10^Y[g][1 + i] for the W entries of pair g (the preconditioner
+// outputs); a non-finite output gives 1 (no scaling of that entry).
+__global__ void precond_from_mlp_kernel(const float *__restrict__ Y, int nout, int64_t pairs, int W,
+                                        float *__restrict__ d) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= pairs * W) return;
+    const int64_t g = e / W;
+    const int i = (int)(e % W);
+    const float y = Y[g * nout + 1 + i];
+    const float v = exp10f(y);
+    d[e] = (isfinite(y) && isfinite(v) && v > 0.f) ? v : 1.0f;
+}
+
 static unsigned blocks_for(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace bs
@@ -361,6 +374,13 @@ bs_status bs_gather_rows(const float *src, const int64_t *idx, int64_t rows, int
     if (rows == 0) return BS_OK;
     bs::gather_rows_kernel<<<bs::blocks_for(rows * cols), 256, 0, (cudaStream_t)stream>>>(src, idx, rows, cols, dst);
     return bs::check_launch("gather");
+}
+
+bs_status bs_precond_from_mlp(const float *Y, int32_t nout, int64_t pairs, int32_t W, float *d, bs_stream stream) {
+    if (!Y || !d || W < 1 || nout < 1 + W || pairs < 0) return set_error(BS_EINVAL, "bad argument");
+    if (pairs == 0) return BS_OK;
+    bs::precond_from_mlp_kernel<<<bs::blocks_for(pairs * W), 256, 0, (cudaStream_t)stream>>>(Y, nout, pairs, W, d);
+    return bs::check_launch("preconditioner from MLP");
 }
 
 bs_status bs_loading_from_mlp(const float *Y, int32_t nout, int64_t pairs, float lo, float hi, float fallback,

@@ -17,7 +17,8 @@ __global__ void __launch_bounds__(SOLVE_PAIRS_PER_CTA * 16, 5)
                       const int32_t *__restrict__ Wg, const int64_t *__restrict__ woff,
                       const float2 *__restrict__ at32, const float2 *__restrict__ atlo,
                       const double2 *__restrict__ at64, float2 *__restrict__ c, int32_t *__restrict__ info,
-                      int64_t pairs, double kappa_max, int refine, int allow_f64, const int32_t *__restrict__ order) {
+                      int64_t pairs, double kappa_max, int refine, int allow_f64, const int32_t *__restrict__ order,
+                      const float *__restrict__ dpre) {
     __shared__ double2 scratch[SOLVE_PAIRS_PER_CTA][WMAX][WMAX + 1];
     const int hw = threadIdx.x >> 4;
     const int lane = threadIdx.x & 15;
@@ -27,7 +28,7 @@ __global__ void __launch_bounds__(SOLVE_PAIRS_PER_CTA * 16, 5)
     const int64_t g = order ? (int64_t)order[slot] : slot;   // pairs grouped by W
     const int64_t wo = woff[g];
     solve_pair(mask, lane, Wg[g], R + roff[g], at32 + wo, atlo + wo, at64 + wo, c + wo, info + g, kappa_max, refine,
-               allow_f64, scratch[hw]);
+               allow_f64, scratch[hw], dpre ? dpre + wo : nullptr);
 }
 
 // Plain FP32 per-pair solve: one thread factorises and solves its pair in
@@ -81,7 +82,8 @@ __global__ void plain_solve_kernel(const double2 *__restrict__ R, const int64_t 
     info[g] = 0;
 }
 
-bs_status launch_mvdr_solve(const bs_plan *p, const double2 *R, float2 *c, int32_t *info, cudaStream_t st) {
+bs_status launch_mvdr_solve(const bs_plan *p, const double2 *R, float2 *c, int32_t *info, cudaStream_t st,
+                            const float *dpre) {
     const int64_t G = p->pairs;
     if (p->Wmax > WMAX) return set_error(BS_EUNSUPPORTED, "W > 16");
     if (p->cfg.flags & BS_FLAG_PLAIN) {
@@ -92,7 +94,7 @@ bs_status launch_mvdr_solve(const bs_plan *p, const double2 *R, float2 *c, int32
     mvdr_solve_kernel<<<blocks, SOLVE_PAIRS_PER_CTA * 16, 0, st>>>(
         R, p->d_roff, p->d_Wg, p->d_woff, p->d_at32, p->d_atlo, p->d_at64, c, info, G, p->cfg.kappa_max,
         (p->cfg.flags & BS_FLAG_NO_REFINE) ? 0 : 1, (p->cfg.flags & BS_FLAG_NO_FP64) ? 0 : 1,
-        p->Wmin == p->Wmax ? nullptr : p->d_order_w);
+        p->Wmin == p->Wmax ? nullptr : p->d_order_w, dpre);
     return check_launch("solve launch");
 }
 

@@ -193,6 +193,11 @@ static bs_status validate_config(const bs_config *cfg) {
     if (c.precision < BS_PREC_FP32 || c.precision > BS_PREC_BF16)
         return set_error(BS_EINVAL, "unknown precision");
     const int B = c.F / c.L;
+    if (c.s_count > 0 && c.s_count < c.L) {
+        if (!is_pow2(c.s_count) || c.s_begin < 0 || c.s_begin % c.s_count || c.s_begin + c.s_count > c.L)
+            return set_error(BS_EINVAL, "subband shard: s_count a power of two, s_begin a multiple of it, "
+                                        "s_begin + s_count <= L");
+    }
     if (c.Nz > 1 || c.Mz > 1) {
         if (c.Nz < 1 || c.N % c.Nz) return set_error(BS_EINVAL, "planar: Nz must divide N");
         if (!is_pow2(c.Mz) || c.Mz < c.Nz || c.M % c.Mz || c.M / c.Mz < c.N / c.Nz)
@@ -217,14 +222,24 @@ static bs_status validate_config(const bs_config *cfg) {
     return BS_OK;
 }
 
+// The plan's subbands: the first and how many (a shard, or all L).
+static void shard_range(const bs_config &c, int *s0, int *Ls) {
+    const bool shard = c.s_count > 0 && c.s_count < c.L;
+    *s0 = shard ? c.s_begin : 0;
+    *Ls = shard ? c.s_count : c.L;
+}
+
 bs_status bs_plan_tables_host(const bs_config *cfg, int32_t *start, bs_cf64 *a_tilde) {
     if (bs_status st = validate_config(cfg)) return st;
     const bs_config &c = *cfg;
     const Geom G = geometry(c);
+    int s0, Ls;
+    shard_range(c, &s0, &Ls);
     int64_t e = 0;
     for (int t = 0; t < c.T; ++t) {
-        for (int s = 0; s < c.L; ++s) {
-            const int64_t g = (int64_t)t * c.L + s;
+        for (int sl = 0; sl < Ls; ++sl) {
+            const int s = s0 + sl;
+            const int64_t g = (int64_t)t * Ls + sl;
             int sx, sz;
             pair_starts(c, G, t, s, &sx, &sz);
             if (start) start[g] = sx;
@@ -259,9 +274,11 @@ bs_status bs_plan_create(bs_plan **out, const bs_config *cfg) {
     if (!(p->cfg.kappa_max > 0)) p->cfg.kappa_max = 1e5;
     if (!(p->cfg.store_scale > 0)) p->cfg.store_scale = 1.0f;
     p->B = B;
+    shard_range(c, &p->s0, &p->Ls);
+    p->Fs = p->Ls * B;
     p->P = c.P_train + c.P_test;
     p->Vte = c.P_test * B;
-    p->pairs = (int64_t)c.T * c.L;
+    p->pairs = (int64_t)c.T * p->Ls;
     p->Wt.assign(c.W, c.W + c.T);
     p->Kt.assign(c.K, c.K + c.T);
     p->u.assign(c.u, c.u + c.T);
@@ -280,8 +297,9 @@ bs_status bs_plan_create(bs_plan **out, const bs_config *cfg) {
     p->zte_off.assign(G + 1, 0);
     p->roff.assign(G + 1, 0);
     for (int t = 0; t < c.T; ++t) {
-        for (int s = 0; s < c.L; ++s) {
-            const int64_t g = (int64_t)t * c.L + s;
+        for (int sl = 0; sl < p->Ls; ++sl) {
+            const int s = p->s0 + sl;
+            const int64_t g = (int64_t)t * p->Ls + sl;
             const int W = p->Wt[t], K = p->Kt[t];
             p->Wg[g] = W;
             p->Kg[g] = K;
@@ -303,8 +321,9 @@ bs_status bs_plan_create(bs_plan **out, const bs_config *cfg) {
     std::vector<float2> at32(p->c_elems), atlo(p->c_elems);
     std::vector<double2> at64(p->c_elems);
     for (int t = 0; t < c.T; ++t) {
-        for (int s = 0; s < c.L; ++s) {
-            const int64_t g = (int64_t)t * c.L + s;
+        for (int sl = 0; sl < p->Ls; ++sl) {
+            const int s = p->s0 + sl;
+            const int64_t g = (int64_t)t * p->Ls + sl;
             for (int w = 0; w < p->Wg[g]; ++w) {
                 const bs_cf64 a = pair_steering(c, geo, t, s, p->start[g], p->start_z[g], w);
                 const int64_t e = p->woff[g] + w;
@@ -321,16 +340,16 @@ bs_status bs_plan_create(bs_plan **out, const bs_config *cfg) {
     p->gather.reserve((size_t)p->vpb * p->sumW);
     for (int t = 0; t < c.T; ++t)
         for (int cc = 0; cc < p->vpb; ++cc)
-            for (int w = 0; w < p->Wt[t]; ++w) p->gather.push_back((t << 8) | (cc << 4) | w);
+            for (int w = 0; w < p->Wt[t]; ++w) p->gather.push_back((t << 10) | (cc << 5) | w);
     p->glist.reserve((size_t)p->sumW);
     for (int t = 0; t < c.T; ++t)
         for (int w = 0; w < p->Wt[t]; ++w) p->glist.push_back((t << 8) | w);
     // the same per-pair fields subband-major, so that the per-group entries
     // of consecutive targets are one contiguous read
     p->gsub.resize((size_t)4 * G);
-    for (int s = 0; s < c.L; ++s)
+    for (int s = 0; s < p->Ls; ++s)
         for (int t = 0; t < c.T; ++t) {
-            const int64_t g = (int64_t)t * c.L + s;
+            const int64_t g = (int64_t)t * p->Ls + s;
             int64_t *e = &p->gsub[(size_t)4 * ((int64_t)s * c.T + t)];
             e[0] = p->ztr_off[g];
             e[1] = p->zte_off[g];
@@ -405,6 +424,13 @@ bs_status bs_plan_device_status(const bs_plan *p, int32_t *flags) {
     return BS_OK;
 }
 
+bs_status bs_plan_set_device_flags(bs_plan *p, int32_t flags) {
+    if (!p) return set_error(BS_EINVAL, "NULL plan");
+    const int h = flags;
+    const cudaError_t e = cudaMemcpy(p->d_err, &h, sizeof(int), cudaMemcpyHostToDevice);
+    return bs::cuda_error(e, "device error word write");
+}
+
 bs_status bs_plan_sizes(const bs_plan *p, bs_sizes *o) {
     if (!p || !o) return set_error(BS_EINVAL, "NULL argument");
     std::memset(o, 0, sizeof(*o));
@@ -414,7 +440,7 @@ bs_status bs_plan_sizes(const bs_plan *p, bs_sizes *o) {
     o->W_max = p->Wmax;
     o->K_max = p->Kmax;
     o->x_elems = (int64_t)p->P * p->cfg.F * p->cfg.N;
-    o->xc_elems = o->x_elems;
+    o->xc_elems = (int64_t)p->P * p->Fs * p->cfg.N;
     o->ztrain_elems = p->ztr_elems;
     o->ztrain_bytes = p->ztr_elems * (p->cfg.precision == BS_PREC_FP32 ? 8 : 4);
     o->ztest_elems = p->zte_elems;

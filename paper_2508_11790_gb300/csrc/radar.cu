@@ -11,8 +11,12 @@
 // * rows: the library's one-shot row FFT (F points, F-point twiddle table).
 // * doppler: map[t][d][tau] = |sum_r rp[t][r][tau] e^{-j 2 pi d r / P_te}|^2
 //   with rp = conj(row FFT output); thread per (t, tau), all d.
-// * cfar: one CTA per target: the mean of its map (FP32 compensated partial
-//   sums, combined in FP64), then the cells above mean x 10^(thr/10).
+// * cfar (Sec. IV-B: a one-dimensional CFAR across the velocity bins): one
+//   CTA per target, a thread per range cell tau: the floor of cell (d, tau)
+//   is the mean of the other P_te - 1 velocity bins of range cell tau (the
+//   cell under test left out), a detection is a cell above its floor x
+//   10^(thr/10) (FP32); the CTA counts the detections and reduces the
+//   strongest one (smallest index on ties) to the target's peak cell.
 #include "common.cuh"
 #include "internal.h"
 
@@ -54,41 +58,58 @@ __global__ void rd_doppler_kernel(const float2 *__restrict__ fr, float *__restri
     }
 }
 
-__global__ void __launch_bounds__(256) rd_cfar_kernel(const float *__restrict__ map, int cells, float ratio,
+__global__ void __launch_bounds__(256) rd_cfar_kernel(const float *__restrict__ map, int P_te, int F, float ratio,
                                                       float *__restrict__ floor_out, int32_t *__restrict__ count,
-                                                      uint8_t *__restrict__ mask) {
+                                                      uint8_t *__restrict__ mask, int32_t *__restrict__ peak) {
     const int t = blockIdx.x;
+    const int64_t cells = (int64_t)P_te * F;
     const float *m = map + (int64_t)t * cells;
-    __shared__ double part[256];
+    __shared__ float best_v[256];
+    __shared__ int best_i[256];
     __shared__ int cnt_s;
-    float hi = 0.f, lo = 0.f;   // compensated sum of this thread's cells
-    for (int c = threadIdx.x; c < cells; c += 256) {
-        const float b = m[c];
-        const float s = hi + b;
-        const float bb = s - hi;
-        lo += (hi - (s - bb)) + (b - bb);
-        hi = s;
-    }
-    part[threadIdx.x] = (double)hi + (double)lo;
     if (threadIdx.x == 0) cnt_s = 0;
     __syncthreads();
-    for (int o = 128; o; o >>= 1) {
-        if (threadIdx.x < o) part[threadIdx.x] += part[threadIdx.x + o];
-        __syncthreads();
+    const float inv = 1.0f / (float)(P_te - 1);
+    float bv = -1.0f;   // map cells are >= 0
+    int bi = -1, mine = 0;
+    for (int tau = threadIdx.x; tau < F; tau += 256) {
+        for (int d = 0; d < P_te; ++d) {
+            float sum = 0.f;   // the other velocity bins of range cell tau, in order
+            for (int e = 0; e < P_te; ++e)
+                if (e != d) sum += m[(int64_t)e * F + tau];
+            const float fl = sum * inv;
+            const int64_t c = (int64_t)d * F + tau;
+            const float v = m[c];
+            const bool hit = v > fl * ratio;
+            floor_out[(int64_t)t * cells + c] = fl;
+            if (mask) mask[(int64_t)t * cells + c] = hit ? 1 : 0;
+            mine += hit;
+            if (hit && (v > bv || (v == bv && (int)c < bi))) {
+                bv = v;
+                bi = (int)c;
+            }
+        }
     }
-    const float fl = (float)(part[0] / (double)cells);
-    const float thr = fl * ratio;
-    int mine = 0;
-    for (int c = threadIdx.x; c < cells; c += 256) {
-        const bool hit = m[c] > thr;
-        mine += hit;
-        if (mask) mask[(int64_t)t * cells + c] = hit ? 1 : 0;
-    }
+    best_v[threadIdx.x] = bv;
+    best_i[threadIdx.x] = bi;
     atomicAdd(&cnt_s, mine);
     __syncthreads();
+    for (int o = 128; o; o >>= 1) {
+        if (threadIdx.x < o) {
+            const float v2 = best_v[threadIdx.x + o];
+            const int i2 = best_i[threadIdx.x + o];
+            const float v1 = best_v[threadIdx.x];
+            const int i1 = best_i[threadIdx.x];
+            if (i2 >= 0 && (i1 < 0 || v2 > v1 || (v2 == v1 && i2 < i1))) {
+                best_v[threadIdx.x] = v2;
+                best_i[threadIdx.x] = i2;
+            }
+        }
+        __syncthreads();
+    }
     if (threadIdx.x == 0) {
-        floor_out[t] = fl;
         count[t] = cnt_s;
+        if (peak) peak[t] = best_i[0];
     }
 }
 
@@ -108,11 +129,11 @@ bs_status launch_range_doppler(const bs_plan *p, const float2 *out, const float2
 }
 
 bs_status launch_cfar(const bs_plan *p, const float *map, float threshold_db, float *floor, int32_t *count,
-                      uint8_t *mask, cudaStream_t st) {
+                      uint8_t *mask, int32_t *peak, cudaStream_t st) {
     const int T = p->cfg.T;
     if (T == 0 || p->cfg.P_test == 0) return BS_OK;
     const float ratio = powf(10.f, threshold_db / 10.f);
-    rd_cfar_kernel<<<T, 256, 0, st>>>(map, p->cfg.P_test * p->cfg.F, ratio, floor, count, mask);
+    rd_cfar_kernel<<<T, 256, 0, st>>>(map, p->cfg.P_test, p->cfg.F, ratio, floor, count, mask, peak);
     return check_launch("CFAR launch");
 }
 

@@ -16,6 +16,12 @@
 // (max L_ii / min L_ii)^2 exceeds kappa_max, is solved again entirely in
 // FP64 (info = -2).  Non-finite input: info = -1, c = NaN.  FP64 pivot k
 // not positive: info = k + 1, c = NaN.
+//
+// Optional diagonal preconditioner d (the learned seed): with D = diag(2^e),
+// e_i the exponent of d_i rounded to the nearest power of two, the solve
+// runs on D R D and D a and returns c = D y / (a^H D y) -- the same c in
+// exact arithmetic, and every scaling is exact (powers of two), so only
+// the conditioning that the Cholesky sees (and the escalation test) change.
 #pragma once
 #include <math.h>
 
@@ -156,14 +162,37 @@ static __device__ __forceinline__ int solve_f64_rows(unsigned mask, int lane, in
     return 0;
 }
 
+// Exponent of the power of two nearest to d in log scale, clamped to
+// [-30, 30]; 0 for non-positive or non-finite d (no scaling).
+__device__ __forceinline__ int precond_exp(float d) {
+    if (!(d > 0.f) || !isfinite(d)) return 0;
+    const unsigned b = __float_as_uint(d);
+    int e = (int)((b >> 23) & 0xFFu) - 127;
+    if (e == -127) return -30;                       // subnormal: as small as allowed
+    if ((b & 0x7FFFFFu) >= 0x3504F3u) e += 1;        // mantissa >= sqrt(2): round up
+    return e < -30 ? -30 : (e > 30 ? 30 : e);
+}
+// 2^e as a float, -126 <= e <= 127
+__device__ __forceinline__ float pow2f(int e) { return __uint_as_float((unsigned)(e + 127) << 23); }
+
 // Not inlined: compiled once per translation unit for every window size.
+// ex: the lane's preconditioner exponent (0 without one); row j scales by
+// 2^(ex_lane + ex_j), exactly.
 static __device__ __noinline__ int solve_f64(unsigned mask, int lane, int W, const double2 *__restrict__ Rg, double2 a,
-                                double2 (*Ld)[WMAX + 1], double2 &c_out) {
+                                double2 (*Ld)[WMAX + 1], double2 &c_out, int ex) {
     double2 D[WMAX];
     const bool row = lane < W;
 #pragma unroll
-    for (int j = 0; j < WMAX; ++j) D[j] = (row && j < W) ? Rg[lane * W + j] : make_double2(0.0, 0.0);
-    return solve_f64_rows(mask, lane, W, D, a, Ld, c_out);
+    for (int j = 0; j < WMAX; ++j) {
+        const int ej = __shfl_sync(mask, ex, j, 16);
+        const double s = (double)pow2f(ex + ej);
+        const double2 r = (row && j < W) ? Rg[lane * W + j] : make_double2(0.0, 0.0);
+        D[j] = make_double2(r.x * s, r.y * s);
+    }
+    const double si = (double)pow2f(ex);
+    const int f = solve_f64_rows(mask, lane, W, D, make_double2(a.x * si, a.y * si), Ld, c_out);
+    c_out = make_double2(c_out.x * si, c_out.y * si);
+    return f;
 }
 
 // Error-free transformations (FP32): a*b = p + e exactly (FMA), a + b = s + t.
@@ -243,11 +272,17 @@ static __device__ __noinline__ void solve_pair_fixed(unsigned mask, int lane, co
                                                      const float2 *__restrict__ alog,
                                                      const double2 *__restrict__ a64g, float2 *__restrict__ c,
                                                      int32_t *__restrict__ info, double kappa_max, int refine,
-                                                     int allow_f64, double2 (*scratch)[WMAX + 1]) {
+                                                     int allow_f64, double2 (*scratch)[WMAX + 1],
+                                                     const float *__restrict__ dg) {
+    const int ex = (dg && lane < WT) ? precond_exp(dg[lane]) : 0;   // this row's scaling exponent
+    int exj[WT];                                                     // every column's
+#pragma unroll
+    for (int j = 0; j < WT; ++j) exj[j] = __shfl_sync(mask, ex, j, 16);
     auto rows = [&](int j) -> float4 {
         const double2 r = Rg[lane * WT + j];
         const float2 x = split_f64(r.x), y = split_f64(r.y);
-        return make_float4(x.x, y.x, x.y, y.y);
+        const float s = pow2f(ex + exj[j]);   // exact: a power of two
+        return make_float4(x.x * s, y.x * s, x.y * s, y.y * s);
     };
     float2(*Lsf)[WMAX + 1] = reinterpret_cast<float2(*)[WMAX + 1]>(&scratch[0][0]);
     constexpr int W = WT;
@@ -268,8 +303,9 @@ static __device__ __noinline__ void solve_pair_fixed(unsigned mask, int lane, co
         A[j] = make_float2(r.x, r.y);
         if constexpr (WT <= kKeepRow) Rrow[j] = r;
     }
-    const float2 ah = row ? a32g[lane] : make_float2(0.f, 0.f);
-    const float2 al = row ? alog[lane] : make_float2(0.f, 0.f);
+    const float sa = pow2f(ex);
+    const float2 ah = row ? cscale(a32g[lane], sa) : make_float2(0.f, 0.f);
+    const float2 al = row ? cscale(alog[lane], sa) : make_float2(0.f, 0.f);
     finite = finite && isfinite(ah.x) && isfinite(ah.y);
     if (!__all_sync(mask, finite)) {
         if (row) c[lane] = make_float2(nanf(""), nanf(""));
@@ -316,7 +352,7 @@ static __device__ __noinline__ void solve_pair_fixed(unsigned mask, int lane, co
         // 4. c = v / (a~^H v)
         const float2 av = row ? conjmul(ah, v) : make_float2(0.f, 0.f);
         const float sr = hw_sumf(mask, av.x), si = hw_sumf(mask, av.y);
-        const float inv = 1.0f / (sr * sr + si * si);
+        const float inv = sa / (sr * sr + si * si);   // c = D y / (b^H y), b = D a
         if (row) c[lane] = make_float2((v.x * sr + v.y * si) * inv, (v.y * sr - v.x * si) * inv);
         if (lane == 0) *info = 0;
         return;
@@ -331,7 +367,7 @@ static __device__ __noinline__ void solve_pair_fixed(unsigned mask, int lane, co
     __syncwarp(mask);
     double2 cd;
     const double2 a64 = row ? a64g[lane] : make_double2(0.0, 0.0);
-    const int f64fail = solve_f64(mask, lane, W, Rg, a64, Ldd, cd);
+    const int f64fail = solve_f64(mask, lane, W, Rg, a64, Ldd, cd, ex);
     if (f64fail) {
         if (row) c[lane] = make_float2(nanf(""), nanf(""));
         if (lane == 0) *info = f64fail;
@@ -347,9 +383,10 @@ __device__ __forceinline__ void solve_pair(unsigned mask, int lane, int W, const
                                            const float2 *__restrict__ a32g, const float2 *__restrict__ alog,
                                            const double2 *__restrict__ a64g, float2 *__restrict__ c,
                                            int32_t *__restrict__ info, double kappa_max, int refine,
-                                           int allow_f64, double2 (*scratch)[WMAX + 1]) {
+                                           int allow_f64, double2 (*scratch)[WMAX + 1],
+                                           const float *__restrict__ dg = nullptr) {
 #define BS_SOLVE_CASE(n) \
-    case n: solve_pair_fixed<n>(mask, lane, Rg, a32g, alog, a64g, c, info, kappa_max, refine, allow_f64, scratch); break;
+    case n: solve_pair_fixed<n>(mask, lane, Rg, a32g, alog, a64g, c, info, kappa_max, refine, allow_f64, scratch, dg); break;
     switch (W) {
         BS_SOLVE_CASE(1) BS_SOLVE_CASE(2) BS_SOLVE_CASE(3) BS_SOLVE_CASE(4)
         BS_SOLVE_CASE(5) BS_SOLVE_CASE(6) BS_SOLVE_CASE(7) BS_SOLVE_CASE(8)

@@ -12,6 +12,7 @@ from .scene import (
     all_configs,
     make_scene,
     pulse,
+    reference_records,
     scaled_config,
 )
 
@@ -22,5 +23,6 @@ __all__ = [
     "all_configs",
     "make_scene",
     "pulse",
+    "reference_records",
     "scaled_config",
 ]

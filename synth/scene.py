@@ -264,12 +264,20 @@ def pulse(F: int) -> np.ndarray:
 
 
 def make_scene(cfg: SceneConfig, keep_interference: bool = False,
-               k_chunk: int = 64) -> Scene:
-    """Synthesise the raw IQ records x[p][t][n] of one workload (seeded)."""
+               k_chunk: int = 64, realisation: int = 0) -> Scene:
+    """Synthesise the raw IQ records x[p][t][n] of one workload (seeded).
+
+    realisation > 0 keeps the geometry of the workload's scene (target and
+    jammer directions, jammer powers) and draws new jammer waveforms, target
+    echoes and noise: an independent realisation of the same scene.
+    """
     cfg.validate()
     N, F, P, J, T = cfg.N, cfg.F, cfg.P, cfg.n_jam, cfg.T
     ss = np.random.SeedSequence(cfg.seed)
     g_geom, g_jam, g_tgt, g_noise, g_vert = [np.random.default_rng(s) for s in ss.spawn(5)]
+    if realisation:
+        g_jam, g_tgt, g_noise = [np.random.default_rng(s)
+                                 for s in np.random.SeedSequence([cfg.seed, int(realisation)]).spawn(3)]
 
     u_t, u_j = _directions(g_geom, T, J, cfg.Nx)
     v_t = v_j = None
@@ -356,3 +364,14 @@ def make_scene(cfg: SceneConfig, keep_interference: bool = False,
     return Scene(cfg=cfg, x=np.ascontiguousarray(x), u_tgt=u_t, u_jam=u_j,
                  jnr_db=jnr, x_interf=x_interf, v_tgt=v_t, v_jam=v_j, tgt_delay=tgt_delay,
                  tgt_doppler=tgt_doppler)
+
+
+def reference_records(cfg: SceneConfig, P_ref: int, realisation: int = 1) -> np.ndarray:
+    """P_ref target-free records [P_ref][F][N] (complex64) of an independent
+    realisation of cfg's scene: the same jammer directions and powers, new
+    jammer waveforms and noise.  They are not used for the weights, so a
+    covariance estimated from them judges output SINR independently of the
+    training data."""
+    need = -(-max(cfg.K) // cfg.B) if cfg.K else 1
+    ref = dataclasses.replace(cfg, P_tr=max(int(P_ref), need), P_te=0)
+    return make_scene(ref, realisation=realisation).x[:P_ref]

@@ -53,7 +53,7 @@ def run_gpu(cfg, x: np.ndarray, u, precision=P.BS_PREC_FP32, flags=0, keep_xc=Tr
     scale = plan_kw.get("store_scale", 0.0) or 1.0
     res = GpuResult(
         plan=plan, off=plan.offsets(),
-        xc=b.xc.cpu().numpy().reshape(cfg.P, cfg.F, cfg.N) if keep_xc else None,
+        xc=b.xc.cpu().numpy().reshape(cfg.P, -1, cfg.N) if keep_xc else None,
         z_train=ztrain_to_complex(plan, b.z_train, scale),
         z_test=b.z_test.cpu().numpy(),
         R=b.R.cpu().numpy(), c=b.c.cpu().numpy(), info=b.info.cpu().numpy(),

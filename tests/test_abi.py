@@ -138,3 +138,39 @@ def test_planar_window_tables_match_oracle(pkg):
                                         O.squinted_omega(float(sc.v_tgt[t]), f, cfg.fd), cfg.Nx, cfg.Nz)
             np.testing.assert_allclose(at[e:e + cfg.W[t]], a, atol=1e-12)
             e += cfg.W[t]
+
+
+@pytest.mark.parametrize("world", [1, 2, 3, 4, 5])
+def test_subband_shard_tables_concatenate(pkg, world):
+    """Plans restricted to aligned power-of-two subband blocks (the blocks of
+    each rank's share, shard_plan_blocks) hold exactly the window starts and
+    steering vectors of the same pairs of the unsharded plan: pair
+    (t, s_begin + j) of a shard is pair t s_count + j of its tables."""
+    from paper_2508_11790_gb300.shard import shard_plan_blocks
+    base = all_configs()["C2"]
+    u = np.sin(np.deg2rad(np.random.default_rng(3).uniform(-60, 60, size=base.T)))
+    start, at = pkg.bs_plan_tables_host(**_kw(base, u))
+    L, T, W = base.L, base.T, np.asarray(base.W)
+    woff = np.concatenate([[0], np.cumsum(np.repeat(W, L))])
+    seen = np.zeros((T, L), bool)
+    for rank in range(world):
+        for s0, n in shard_plan_blocks(L, world, rank):
+            st, a = pkg.bs_plan_tables_host(**_kw(base, u, s_begin=s0, s_count=n))
+            assert st.shape == (T * n,)
+            wo = np.concatenate([[0], np.cumsum(np.repeat(W, n))])
+            for t in range(T):
+                for j in range(n):
+                    g, gl = t * L + s0 + j, t * n + j
+                    assert st[gl] == start[g]
+                    assert np.array_equal(a[wo[gl]:wo[gl + 1]], at[woff[g]:woff[g + 1]])
+                    assert not seen[t, s0 + j]
+                    seen[t, s0 + j] = True
+    assert seen.all()
+
+
+@pytest.mark.parametrize("s_begin,s_count", [(2, 4), (0, 3), (-4, 4), (60, 8)])
+def test_subband_shard_validation(pkg, s_begin, s_count):
+    """A shard must be an aligned power-of-two block inside the L subbands."""
+    base = all_configs()["C2"]
+    with pytest.raises(pkg.BsError):
+        pkg.bs_plan_tables_host(**_kw(base, s_begin=s_begin, s_count=s_count))

@@ -99,3 +99,23 @@ def test_loading_targets():
     R = np.diag([1.0, 3.0]).astype(complex)
     t = LL.loading_targets(R, 1.0)
     np.testing.assert_allclose(t, [0.0, math.log10(2 ** -0.5), math.log10(4 ** -0.5)], atol=1e-15)
+
+
+def test_preconditioned_mvdr_is_invariant_and_equilibrates():
+    """The scaled solve gives the plain MVDR correlator for any positive d
+    (exact-arithmetic invariance, to FP64 rounding); d = 1 is the plain
+    solve; Jacobi scaling d = diag(R)^-1/2 gives a unit diagonal and, for a
+    badly scaled R, a far smaller condition number."""
+    W = 9
+    Z = crandn(40, W) * np.logspace(0, 3, W)[None, :]      # columns 1 .. 1000 in scale
+    R = O.window_covariance(Z, 0.5)
+    a = crandn(W)
+    c = O.mvdr_weights(R, a)
+    for d in (np.ones(W), np.exp(RNG.standard_normal(W)), 2.0 ** RNG.integers(-9, 9, size=W)):
+        np.testing.assert_allclose(LL.mvdr_weights_preconditioned(R, a, d), c, rtol=0, atol=1e-9 * np.abs(c).max())
+    dj = np.real(np.diag(R)) ** -0.5
+    Rs = dj[:, None] * R * dj[None, :]
+    np.testing.assert_allclose(np.real(np.diag(Rs)), 1.0, atol=1e-14)
+    assert np.linalg.cond(Rs) < 1e-3 * np.linalg.cond(R)
+    with pytest.raises(ValueError):
+        LL.mvdr_weights_preconditioned(R, a, -np.ones(W))

@@ -54,11 +54,45 @@ def test_range_profile_of_unit_spectrum_is_the_pulse_autocorrelation():
     np.testing.assert_allclose(rp, acf, atol=1e-12)
 
 
-def test_cfar_threshold_and_floor():
-    m = np.ones((2, 4, 8))
-    m[0, 1, 2] = 20.0     # floor (31 + 20) / 32 = 1.59: threshold 15.9
-    m[1, 3, 7] = 12.0     # floor (31 + 12) / 32 = 1.34: threshold 13.4
+def _read_cfar_golden(path):
+    rows = [[float(v) for v in l.split()] for l in open(path) if l.strip() and not l.startswith("#")]
+    return np.array(rows)
+
+
+def test_cfar_across_velocity_bins_golden(golden):
+    """Hand-worked 1-D CFAR (Sec. IV-B) on a 4-velocity-bin x 3-range-cell
+    map: each cell against the mean of the other velocity bins of its
+    range cell."""
+    tab = _read_cfar_golden(golden("cfar_P4_F3.txt"))
+    m = tab[:, 2].reshape(1, 4, 3)
     mask, floor = RD.cfar_detect(m, 10.0)
-    assert floor[0] == pytest.approx((31 + 20.0) / 32) and floor[1] == pytest.approx((31 + 12.0) / 32)
-    assert mask[0].sum() == 1 and mask[0, 1, 2]
-    assert mask[1].sum() == 0
+    np.testing.assert_allclose(floor.reshape(-1), tab[:, 3], rtol=1e-15)
+    assert (mask.reshape(-1) == tab[:, 4].astype(bool)).all()
+
+
+def test_cfar_target_alone_in_its_range_cell_is_detected():
+    """With the cell under test left out of its own floor, a target 20 dB
+    above flat noise is detected at P_te = 4..8 (a floor that included it
+    would reach m / P_te + noise and hide it at 10 dB for P_te <= 10), and
+    nothing else is."""
+    for Pd in (4, 5, 8):
+        m = np.ones((1, Pd, 16))
+        m[0, Pd - 1, 9] = 100.0
+        mask, floor = RD.cfar_detect(m, 10.0)
+        assert mask.sum() == 1 and mask[0, Pd - 1, 9]
+        assert floor[0, Pd - 1, 9] == pytest.approx(1.0)
+        assert floor[0, 0, 9] == pytest.approx((Pd - 2 + 100.0) / (Pd - 1))
+    with pytest.raises(ValueError):
+        RD.cfar_detect(np.ones((1, 1, 4)))
+
+
+def test_detection_errors():
+    m = np.ones((3, 4, 10))
+    mask = np.zeros(m.shape, bool)
+    m[0, 1, 6] = 50.0; mask[0, 1, 6] = True          # exact
+    m[1, 3, 2] = 30.0; mask[1, 3, 2] = True          # velocity wraps: 3 - 0 -> -1
+    m[1, 2, 2] = 40.0; mask[1, 2, 2] = True          # the stronger detection wins
+    det = RD.detection_errors(mask, m, delay=[6, 4, 0], doppler=[1, 0, 0])
+    assert det[0] == (True, (1, 6), 0, 0)
+    assert det[1] == (True, (2, 2), -2, 2 - 4)
+    assert det[2] == (False, None, None, None)
