@@ -48,6 +48,7 @@ _SIGS = {
     "bs_gather_rows": ([_P, _P, ctypes.c_int64, ctypes.c_int32, _P, _P], ctypes.c_int),
     "bs_loading_from_mlp": ([_P, ctypes.c_int32, ctypes.c_int64, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                              _P, _P], ctypes.c_int),
+    "bs_precond_from_mlp": ([_P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, _P, _P], ctypes.c_int),
 }
 _bound = False
 
@@ -139,6 +140,13 @@ class LoadingMLP:
             b = min(self.capacity, n - s)
             self.forward(X[s * self.n_in:], b, Y[s * self.n_out:], stream)
         return Y
+
+    def precond(self, Y: torch.Tensor, n: int, W: int, stream=None) -> torch.Tensor:
+        """The preconditioner seed d [n * W] (10^ of outputs 1..W)."""
+        d = torch.empty(n * W, dtype=torch.float32, device=Y.device)
+        _check(_lib().bs_precond_from_mlp(_ptr(Y, torch.float32, n * self.n_out, "Y"), self.n_out, n, W,
+                                          d.data_ptr(), _stream(stream)), "bs_precond_from_mlp")
+        return d
 
     def loading(self, Y: torch.Tensor, n: int, lo=0.1, hi=1e4, fallback=10.0, stream=None) -> torch.Tensor:
         d = torch.empty(n, dtype=torch.float32, device=Y.device)
@@ -244,9 +252,18 @@ def evaluate_scene(cfg, x: np.ndarray, u, K_small: int, mlp: LoadingMLP, base_de
                    device="cuda") -> dict:
     """Runs the path on one scene with the network's per-pair loading and with
     the fixed loading base_delta; both weight sets are judged by the output
-    SINR against the reference covariance (K_ref = P_tr * B vectors).
-    Returns per-pair SINRs (numpy) and the mean gain in dB."""
-    from . import (alloc_buffers, bs_beamspace, bs_channelize, bs_mvdr_solve, bs_window_cov)
+    SINR against the reference covariance (K_ref = P_tr * B vectors).  The
+    learned loading is solved twice more with the network's preconditioner
+    seed and with exact Jacobi scaling (diag(R + delta)^-1/2): their weights
+    are compared with the unscaled solve's (the scaling is by powers of two,
+    under which the FP32 Cholesky is exactly equivariant, so pairs solved in
+    FP32 both ways agree bit for bit), the FP64 escalations (info = -2) of
+    each are counted, and for the pairs that only the scaled pivot test
+    escalates, the distance of the unscaled FP32 weights from the FP64 ones
+    is reported.  Returns per-pair SINRs (numpy), the mean gain in dB and
+    those counts."""
+    from . import (alloc_buffers, bs_beamspace, bs_channelize, bs_mvdr_solve, bs_mvdr_solve_precond,
+                   bs_window_cov)
     W = int(cfg.W[0])
     T = cfg.T
     B = cfg.F // cfg.L
@@ -271,6 +288,7 @@ def evaluate_scene(cfg, x: np.ndarray, u, K_small: int, mlp: LoadingMLP, base_de
     _check(L.bs_features(ps.handle, Ru.data_ptr(), X.data_ptr(), _stream(None)), "bs_features")
     Y = mlp.predict(X, G)
     dhat = mlp.loading(Y, G, fallback=base_delta)
+    seed = mlp.precond(Y, G, W)
     out = {}
     for name, dpair in (("learned", dhat), ("fixed", None)):
         bs_window_cov(ps, b.z_train, b.R, delta_pair=dpair)
@@ -279,6 +297,29 @@ def evaluate_scene(cfg, x: np.ndarray, u, K_small: int, mlp: LoadingMLP, base_de
         _check(L.bs_output_sinr(ps.handle, b.c.data_ptr(), Rr.data_ptr(), s.data_ptr(), _stream(None)),
                "bs_output_sinr")
         out[name] = s.cpu().numpy()
+        out["escalations_" + name] = int((b.info == -2).sum().item())
+    # the learned loading again (b.R holds the fixed loading now)
+    bs_window_cov(ps, b.z_train, b.R, delta_pair=dhat)
+    bs_mvdr_solve(ps, b.R, b.c, b.info)
+    c_plain, info_plain = b.c.clone(), b.info.clone()
+    Rd = b.R.view(G, W, W).diagonal(dim1=1, dim2=2).real
+    jacobi = Rd.clamp_min(1e-30).rsqrt().to(torch.float32).reshape(-1).contiguous()
+    for name, dvec in (("seed", seed), ("jacobi", jacobi)):
+        c2 = torch.empty_like(b.c)
+        info2 = torch.empty_like(b.info)
+        bs_mvdr_solve_precond(ps, b.R, dvec, c2, info2)
+        both = ((info2 == 0) & (info_plain == 0)).repeat_interleave(W)
+        diff = (c2 - c_plain).abs().view(G, W).norm(dim=1) / c_plain.view(G, W).abs().norm(dim=1)
+        out["escalations_learned_" + name] = int((info2 == -2).sum().item())
+        out["max_weight_change_" + name] = float(diff[both.view(G, W)[:, 0]].max().item()) if both.any() else 0.0
+        # pairs the scaled pivot test sends to FP64 that the unscaled test
+        # left in FP32: how far the FP32 weights were from the FP64 ones
+        moved = ((info2 == -2) & (info_plain == 0))
+        out["fp32_error_where_" + name + "_escalates"] = float(diff[moved].max().item()) if moved.any() else 0.0
+        # pairs the scaled pivot test sends to FP64 that the unscaled test
+        # left in FP32: how far the FP32 weights were from the FP64 ones
+        moved = ((info2 == -2) & (info_plain == 0))
+        out["fp32_error_where_" + name + "_escalates"] = float(diff[moved].max().item()) if moved.any() else 0.0
     out["delta_hat"] = dhat.cpu().numpy()
     out["gain_db"] = float(np.mean(10.0 * np.log10(out["learned"] / out["fixed"])))
     return out
