@@ -12,14 +12,20 @@
 
 namespace bs {
 
-constexpr int APPLY_THREADS = 256;
-constexpr int APPLY_SPAN = 32 * 16;   // float2 per warp: 32 outputs x W <= 16
+// WM: the largest window (16, or 32 with half as many warps per CTA), so a
+// warp's span of 32 outputs x W_g entries fits its shared-memory buffer.
+template <int WM>
+struct ApplyCfg {
+    static constexpr int threads = WM <= 16 ? 256 : 128;
+    static constexpr int span = 32 * WM;   // float2 per warp
+};
 
-__global__ void __launch_bounds__(APPLY_THREADS)
+template <int WM>
+__global__ void __launch_bounds__(ApplyCfg<WM>::threads)
     apply_kernel(const float2 *__restrict__ z, const int64_t *__restrict__ zte_off,
                  const int32_t *__restrict__ Wg, const int64_t *__restrict__ woff,
                  const float2 *__restrict__ c, float2 *__restrict__ out, int64_t total, int Vte) {
-    __shared__ float2 span[APPLY_THREADS / 32][APPLY_SPAN];
+    __shared__ float2 span[ApplyCfg<WM>::threads / 32][ApplyCfg<WM>::span];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t idx0 = (int64_t)blockIdx.x * blockDim.x + warp * 32;
     if (idx0 >= total) return;   // uniform per warp
@@ -32,7 +38,7 @@ __global__ void __launch_bounds__(APPLY_THREADS)
     const int64_t start = __ldg(&zte_off[g]) + (int64_t)v * W;
     const int64_t s0 = __shfl_sync(0xFFFFFFFFu, start, 0);
     const int64_t e31 = __shfl_sync(0xFFFFFFFFu, start + W, 31);
-    const int n = (int)(e31 - s0);   // <= 32 * 16
+    const int n = (int)(e31 - s0);   // <= 32 * WM
     float2 *buf = span[warp];
     for (int e = lane; e < n; e += 32) buf[e] = __ldcs(&z[s0 + e]);
     __syncwarp();
@@ -52,9 +58,16 @@ __global__ void __launch_bounds__(APPLY_THREADS)
 bs_status launch_apply(const bs_plan *p, const float2 *zte, const float2 *c, float2 *out, cudaStream_t st) {
     const int64_t total = p->pairs * p->Vte;
     if (total == 0) return BS_OK;
-    if (p->Wmax > 16) return set_error(BS_EUNSUPPORTED, "W > 16");
-    const int64_t blocks = (total + APPLY_THREADS - 1) / APPLY_THREADS;
-    apply_kernel<<<(unsigned)blocks, APPLY_THREADS, 0, st>>>(zte, p->d_zte_off, p->d_Wg, p->d_woff, c, out, total, p->Vte);
+    if (p->Wmax > 32) return set_error(BS_EUNSUPPORTED, "W > 32");
+    if (p->Wmax <= 16) {
+        constexpr int thr = ApplyCfg<16>::threads;
+        apply_kernel<16><<<(unsigned)((total + thr - 1) / thr), thr, 0, st>>>(zte, p->d_zte_off, p->d_Wg, p->d_woff, c,
+                                                                             out, total, p->Vte);
+    } else {
+        constexpr int thr = ApplyCfg<32>::threads;
+        apply_kernel<32><<<(unsigned)((total + thr - 1) / thr), thr, 0, st>>>(zte, p->d_zte_off, p->d_Wg, p->d_woff, c,
+                                                                             out, total, p->Vte);
+    }
     return check_launch("apply launch");
 }
 

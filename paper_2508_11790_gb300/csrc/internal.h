@@ -66,6 +66,7 @@ struct bs_plan {
     std::vector<int32_t> order_w;
     int32_t *d_order_w = nullptr;
     int Wmin = 0;
+    int64_t nsmall = 0;   // pairs with W <= 16 (the first of order_w)
     int *d_head = nullptr;
     bs::CovSolveLaunch cs;
 };

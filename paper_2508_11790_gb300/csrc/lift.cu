@@ -29,7 +29,7 @@ __global__ void __launch_bounds__(256)
                 float2 *__restrict__ c_hat) {
     const int64_t g = blockIdx.x;
     const int n = blockIdx.y * blockDim.x + threadIdx.x;
-    __shared__ float2 cw[16];
+    __shared__ float2 cw[32];
     const int W = Wg[g];
     if (threadIdx.x < W) cw[threadIdx.x] = c[woff[g] + threadIdx.x];
     __syncthreads();
@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(256)
 bs_status launch_lift(const bs_plan *p, const float2 *c, float2 *c_hat, cudaStream_t st) {
     const int N = p->cfg.N;
     if (p->pairs == 0) return BS_OK;
-    if (p->Wmax > 16) return set_error(BS_EUNSUPPORTED, "W > 16");
+    if (p->Wmax > 32) return set_error(BS_EUNSUPPORTED, "W > 32");
     dim3 grid((unsigned)p->pairs, (N + 255) / 256);
     lift_kernel<<<grid, 256, 0, st>>>(c, p->d_woff, p->d_Wg, p->d_start, p->d_twM, p->cfg.M, N,
                                       1.0f / sqrtf((float)p->cfg.M), c_hat);

@@ -212,7 +212,7 @@ static bs_status validate_config(const bs_config *cfg) {
         }
     }
     for (int t = 0; t < c.T; ++t) {
-        if (c.W[t] < 1 || c.W[t] > 16) return set_error(BS_EUNSUPPORTED, "window sizes must be in 1..16");
+        if (c.W[t] < 1 || c.W[t] > 32) return set_error(BS_EUNSUPPORTED, "window sizes must be in 1..32");
         if (c.W[t] > c.M) return set_error(BS_EINVAL, "window larger than M");
         if (c.K[t] < 1 || (int64_t)c.K[t] > (int64_t)c.P_train * B)
             return set_error(BS_EINVAL, "K must be in 1..P_train*B");
@@ -371,6 +371,7 @@ bs_status bs_plan_create(bs_plan **out, const bs_config *cfg) {
     std::stable_sort(p->order_w.begin(), p->order_w.end(),
                      [&](int32_t x, int32_t y) { return p->Wg[x] < p->Wg[y]; });
     p->Wmin = *std::min_element(p->Wg.begin(), p->Wg.end());
+    p->nsmall = std::count_if(p->Wg.begin(), p->Wg.end(), [](int32_t w) { return w <= 16; });
 
     cudaGetDevice(&p->device);
     bs_status st = BS_OK;

@@ -29,7 +29,8 @@
 
 namespace bs {
 
-constexpr int WMAX = 16;
+constexpr int WMAX = 16;        // half-warp solve: W <= 16
+constexpr int WMAX_WIDE = 32;   // whole-warp solve: 16 < W <= 32
 
 __device__ __forceinline__ float2 conjmul(float2 l, float2 v) {   // conj(l) * v
     return make_float2(l.x * v.x + l.y * v.y, l.x * v.y - l.y * v.x);
@@ -43,24 +44,28 @@ __device__ __forceinline__ double2 dcmulc(double2 a, double2 b) {  // a * conj(b
 __device__ __forceinline__ double2 dconjmul(double2 l, double2 v) {  // conj(l) * v
     return make_double2(l.x * v.x + l.y * v.y, l.x * v.y - l.y * v.x);
 }
+// GW: lanes of the group that solves one pair (16: a half-warp for W <= 16;
+// 32: a whole warp for 16 < W <= 32).
+template <int GW = 16>
 __device__ __forceinline__ float2 shfl2(unsigned mask, float2 v, int src) {
-    return make_float2(__shfl_sync(mask, v.x, src, 16), __shfl_sync(mask, v.y, src, 16));
+    return make_float2(__shfl_sync(mask, v.x, src, GW), __shfl_sync(mask, v.y, src, GW));
 }
+template <int GW = 16>
 __device__ __forceinline__ double2 shfl2d(unsigned mask, double2 v, int src) {
-    return make_double2(__shfl_sync(mask, v.x, src, 16), __shfl_sync(mask, v.y, src, 16));
+    return make_double2(__shfl_sync(mask, v.x, src, GW), __shfl_sync(mask, v.y, src, GW));
 }
 
 // FP32 triangular solves with the factor held as rows (A, diag) and its
 // transpose in Ls: returns v = L^-H L^-1 b.  WT = window size.
-template <int WT>
+template <int WT, int GW = 16>
 __device__ __forceinline__ float2 chol_solve_f32(unsigned mask, int lane, const float2 (&A)[WT], float diag,
-                                                 const float2 (*Ls)[WMAX + 1], float2 b) {
+                                                 const float2 (*Ls)[GW + 1], float2 b) {
     const float rdiag = 1.0f / diag;
     float2 acc = b, u = make_float2(0.f, 0.f);
 #pragma unroll
     for (int j = 0; j < WT; ++j) {
         const float2 mine = (lane == j) ? cscale(acc, rdiag) : make_float2(0.f, 0.f);
-        const float2 uj = shfl2(mask, mine, j);
+        const float2 uj = shfl2<GW>(mask, mine, j);
         if (lane == j) u = uj;
         if (lane > j) acc = csub(acc, cmul(A[j], uj));
     }
@@ -69,47 +74,50 @@ __device__ __forceinline__ float2 chol_solve_f32(unsigned mask, int lane, const 
 #pragma unroll
     for (int j = WT - 1; j >= 0; --j) {
         const float2 mine = (lane == j) ? cscale(acc, rdiag) : make_float2(0.f, 0.f);
-        const float2 vj = shfl2(mask, mine, j);
+        const float2 vj = shfl2<GW>(mask, mine, j);
         if (lane == j) v = vj;
         if (lane < j) acc = csub(acc, conjmul(Ls[j][lane], vj));
     }
     return v;
 }
 
+template <int GW = 16>
 __device__ __forceinline__ double hw_sum(unsigned mask, double x) {
 #pragma unroll
-    for (int o = 8; o > 0; o >>= 1) x += __shfl_xor_sync(mask, x, o, 16);
+    for (int o = GW / 2; o > 0; o >>= 1) x += __shfl_xor_sync(mask, x, o, GW);
     return x;
 }
+template <int GW = 16>
 __device__ __forceinline__ float hw_sumf(unsigned mask, float x) {
 #pragma unroll
-    for (int o = 8; o > 0; o >>= 1) x += __shfl_xor_sync(mask, x, o, 16);
+    for (int o = GW / 2; o > 0; o >>= 1) x += __shfl_xor_sync(mask, x, o, GW);
     return x;
 }
 
 // Whole solve in FP64 for one pair (escalation path), row `lane` of R given
 // in D.  Returns 0 or pivot+1.
-static __device__ __forceinline__ int solve_f64_rows(unsigned mask, int lane, int W, double2 (&D)[WMAX], double2 a,
-                                     double2 (*Ld)[WMAX + 1], double2 &c_out) {
+template <int GW = 16>
+static __device__ __forceinline__ int solve_f64_rows(unsigned mask, int lane, int W, double2 (&D)[GW], double2 a,
+                                     double2 (*Ld)[GW + 1], double2 &c_out) {
     const bool row = lane < W;
 #pragma unroll
-    for (int j = 0; j < WMAX; ++j)
+    for (int j = 0; j < GW; ++j)
         if (!(row && j < W)) D[j] = make_double2(0.0, 0.0);
     int fail = 0;
     double diag = 1.0;
 #pragma unroll
-    for (int k = 0; k < WMAX; ++k) {
+    for (int k = 0; k < GW; ++k) {
         if (k < W) {
-            const double dkk = __shfl_sync(mask, D[k].x, k, 16);
+            const double dkk = __shfl_sync(mask, D[k].x, k, GW);
             if (!(dkk > 0.0) && fail == 0) fail = k + 1;
             const double inv = rsqrt(dkk > 0.0 ? dkk : 1.0);   // one sequence instead of sqrt and a division
             const double pk = (dkk > 0.0 ? dkk : 1.0) * inv;
             if (lane > k) D[k] = make_double2(D[k].x * inv, D[k].y * inv);
             if (lane == k) { D[k] = make_double2(pk, 0.0); diag = pk; }
 #pragma unroll
-            for (int j = k + 1; j < WMAX; ++j) {
+            for (int j = k + 1; j < GW; ++j) {
                 if (j < W) {
-                    const double2 ljk = shfl2d(mask, D[k], j);
+                    const double2 ljk = shfl2d<GW>(mask, D[k], j);
                     if (lane >= j) {
                         const double2 t = dcmulc(D[k], ljk);
                         D[j] = make_double2(D[j].x - t.x, D[j].y - t.y);
@@ -120,7 +128,7 @@ static __device__ __forceinline__ int solve_f64_rows(unsigned mask, int lane, in
     }
     if (fail) return fail;
 #pragma unroll
-    for (int j = 0; j < WMAX; ++j)
+    for (int j = 0; j < GW; ++j)
         if (row && j <= lane) Ld[lane][j] = D[j];
     __syncwarp(mask);
     // one FP64 division per lane: GB300's FP64 pipe is narrow and a division
@@ -128,10 +136,10 @@ static __device__ __forceinline__ int solve_f64_rows(unsigned mask, int lane, in
     const double rdiag = 1.0 / diag;
     double2 acc = a, u = make_double2(0.0, 0.0);
 #pragma unroll
-    for (int j = 0; j < WMAX; ++j) {
+    for (int j = 0; j < GW; ++j) {
         if (j < W) {
             const double2 mine = (lane == j) ? make_double2(acc.x * rdiag, acc.y * rdiag) : make_double2(0.0, 0.0);
-            const double2 uj = shfl2d(mask, mine, j);
+            const double2 uj = shfl2d<GW>(mask, mine, j);
             if (lane == j) u = uj;
             if (lane > j) {
                 const double2 t = dcmul(D[j], uj);
@@ -142,10 +150,10 @@ static __device__ __forceinline__ int solve_f64_rows(unsigned mask, int lane, in
     acc = u;
     double2 v = make_double2(0.0, 0.0);
 #pragma unroll
-    for (int j = WMAX - 1; j >= 0; --j) {
+    for (int j = GW - 1; j >= 0; --j) {
         if (j < W) {
             const double2 mine = (lane == j) ? make_double2(acc.x * rdiag, acc.y * rdiag) : make_double2(0.0, 0.0);
-            const double2 vj = shfl2d(mask, mine, j);
+            const double2 vj = shfl2d<GW>(mask, mine, j);
             if (lane == j) v = vj;
             if (lane < j) {
                 const double2 t = dconjmul(Ld[j][lane], vj);
@@ -155,7 +163,7 @@ static __device__ __forceinline__ int solve_f64_rows(unsigned mask, int lane, in
     }
     // s = a^H v
     const double2 av = dconjmul(a, v);
-    const double sr = hw_sum(mask, row ? av.x : 0.0), si = hw_sum(mask, row ? av.y : 0.0);
+    const double sr = hw_sum<GW>(mask, row ? av.x : 0.0), si = hw_sum<GW>(mask, row ? av.y : 0.0);
     const double rden = 1.0 / (sr * sr + si * si);
     // v / s = v conj(s) / |s|^2
     c_out = make_double2((v.x * sr + v.y * si) * rden, (v.y * sr - v.x * si) * rden);
@@ -178,19 +186,20 @@ __device__ __forceinline__ float pow2f(int e) { return __uint_as_float((unsigned
 // Not inlined: compiled once per translation unit for every window size.
 // ex: the lane's preconditioner exponent (0 without one); row j scales by
 // 2^(ex_lane + ex_j), exactly.
+template <int GW = 16>
 static __device__ __noinline__ int solve_f64(unsigned mask, int lane, int W, const double2 *__restrict__ Rg, double2 a,
-                                double2 (*Ld)[WMAX + 1], double2 &c_out, int ex) {
-    double2 D[WMAX];
+                                double2 (*Ld)[GW + 1], double2 &c_out, int ex) {
+    double2 D[GW];
     const bool row = lane < W;
 #pragma unroll
-    for (int j = 0; j < WMAX; ++j) {
-        const int ej = __shfl_sync(mask, ex, j, 16);
+    for (int j = 0; j < GW; ++j) {
+        const int ej = __shfl_sync(mask, ex, j, GW);
         const double s = (double)pow2f(ex + ej);
         const double2 r = (row && j < W) ? Rg[lane * W + j] : make_double2(0.0, 0.0);
         D[j] = make_double2(r.x * s, r.y * s);
     }
     const double si = (double)pow2f(ex);
-    const int f = solve_f64_rows(mask, lane, W, D, make_double2(a.x * si, a.y * si), Ld, c_out);
+    const int f = solve_f64_rows<GW>(mask, lane, W, D, make_double2(a.x * si, a.y * si), Ld, c_out);
     c_out = make_double2(c_out.x * si, c_out.y * si);
     return f;
 }
@@ -211,13 +220,13 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &t) {
 // split exactly into value + error and summed with two-sum, so r carries
 // about twice the FP32 precision (the refinement then converges like one
 // with an FP64 residual).
-template <int WT, class Rows>
+template <int WT, int GW, class Rows>
 __device__ __forceinline__ float2 residual_df(unsigned mask, int lane, Rows rows, float2 ah, float2 al, float2 v) {
     float sr = ah.x, si = ah.y, cr = al.x, ci = al.y;
     const bool row = lane < WT;
 #pragma unroll
     for (int j = 0; j < WT; ++j) {
-        const float2 vj = shfl2(mask, v, j);
+        const float2 vj = shfl2<GW>(mask, v, j);
         const float4 r4 = row ? rows(j) : make_float4(0.f, 0.f, 0.f, 0.f);
         const float2 Rh = make_float2(r4.x, r4.y), Rl = make_float2(r4.z, r4.w);
         float p1, e1, p2, e2, p3, e3, p4, e4, t;
@@ -266,25 +275,25 @@ __device__ __forceinline__ float2 split_f64(double d) {
 // vector as hi / lo FP32 parts, a64 in FP64 (escalation).  scratch: [16][17]
 // double2 per half-warp.  Writes c[0..W) and *info.  Not inlined, so each
 // window size is compiled once per translation unit.
-template <int WT>
+template <int WT, int GW = 16>
 static __device__ __noinline__ void solve_pair_fixed(unsigned mask, int lane, const double2 *Rg,
                                                      const float2 *__restrict__ a32g,
                                                      const float2 *__restrict__ alog,
                                                      const double2 *__restrict__ a64g, float2 *__restrict__ c,
                                                      int32_t *__restrict__ info, double kappa_max, int refine,
-                                                     int allow_f64, double2 (*scratch)[WMAX + 1],
+                                                     int allow_f64, double2 (*scratch)[GW + 1],
                                                      const float *__restrict__ dg) {
     const int ex = (dg && lane < WT) ? precond_exp(dg[lane]) : 0;   // this row's scaling exponent
     int exj[WT];                                                     // every column's
 #pragma unroll
-    for (int j = 0; j < WT; ++j) exj[j] = __shfl_sync(mask, ex, j, 16);
+    for (int j = 0; j < WT; ++j) exj[j] = __shfl_sync(mask, ex, j, GW);
     auto rows = [&](int j) -> float4 {
         const double2 r = Rg[lane * WT + j];
         const float2 x = split_f64(r.x), y = split_f64(r.y);
         const float s = pow2f(ex + exj[j]);   // exact: a power of two
         return make_float4(x.x * s, y.x * s, x.y * s, y.y * s);
     };
-    float2(*Lsf)[WMAX + 1] = reinterpret_cast<float2(*)[WMAX + 1]>(&scratch[0][0]);
+    float2(*Lsf)[GW + 1] = reinterpret_cast<float2(*)[GW + 1]>(&scratch[0][0]);
     constexpr int W = WT;
     const bool row = lane < W;
 
@@ -318,7 +327,7 @@ static __device__ __noinline__ void solve_pair_fixed(unsigned mask, int lane, co
     float diag = 1.f, dmax = 0.f, dmin = INFINITY;
 #pragma unroll
     for (int k = 0; k < WT; ++k) {
-        const float dkk = __shfl_sync(mask, A[k].x, k, 16);
+        const float dkk = __shfl_sync(mask, A[k].x, k, GW);
         if (!(dkk > 0.f) && fail == 0) fail = k + 1;
         const float inv = rsqrtf(dkk > 0.f ? dkk : 1.f);   // the refinement step absorbs its last-bit error
         const float pk = (dkk > 0.f ? dkk : 1.f) * inv;
@@ -328,7 +337,7 @@ static __device__ __noinline__ void solve_pair_fixed(unsigned mask, int lane, co
         if (lane == k) { A[k] = make_float2(pk, 0.f); diag = pk; }
 #pragma unroll
         for (int j = k + 1; j < WT; ++j) {
-            const float2 ljk = shfl2(mask, A[k], j);
+            const float2 ljk = shfl2<GW>(mask, A[k], j);
             if (lane >= j) A[j] = csub(A[j], cmulc(A[k], ljk));
         }
     }
@@ -340,18 +349,18 @@ static __device__ __noinline__ void solve_pair_fixed(unsigned mask, int lane, co
             if (row && j <= lane) Lsf[lane][j] = A[j];
         __syncwarp(mask);
         // 2. solve in FP32
-        float2 v = chol_solve_f32<WT>(mask, lane, A, diag, Lsf, ah);
+        float2 v = chol_solve_f32<WT, GW>(mask, lane, A, diag, Lsf, ah);
         // 3. refinement with a compensated (double-float) residual
         if (refine) {
             float2 r;
-            if constexpr (WT <= kKeepRow) r = residual_df<WT>(mask, lane, [&](int j) { return Rrow[j]; }, ah, al, v);
-            else r = residual_df<WT>(mask, lane, rows, ah, al, v);
-            const float2 dv = chol_solve_f32<WT>(mask, lane, A, diag, Lsf, r);
+            if constexpr (WT <= kKeepRow) r = residual_df<WT, GW>(mask, lane, [&](int j) { return Rrow[j]; }, ah, al, v);
+            else r = residual_df<WT, GW>(mask, lane, rows, ah, al, v);
+            const float2 dv = chol_solve_f32<WT, GW>(mask, lane, A, diag, Lsf, r);
             v = cadd(v, dv);
         }
         // 4. c = v / (a~^H v)
         const float2 av = row ? conjmul(ah, v) : make_float2(0.f, 0.f);
-        const float sr = hw_sumf(mask, av.x), si = hw_sumf(mask, av.y);
+        const float sr = hw_sumf<GW>(mask, av.x), si = hw_sumf<GW>(mask, av.y);
         const float inv = sa / (sr * sr + si * si);   // c = D y / (b^H y), b = D a
         if (row) c[lane] = make_float2((v.x * sr + v.y * si) * inv, (v.y * sr - v.x * si) * inv);
         if (lane == 0) *info = 0;
@@ -363,11 +372,11 @@ static __device__ __noinline__ void solve_pair_fixed(unsigned mask, int lane, co
         return;
     }
     // FP64 path
-    double2(*Ldd)[WMAX + 1] = scratch;
+    double2(*Ldd)[GW + 1] = scratch;
     __syncwarp(mask);
     double2 cd;
     const double2 a64 = row ? a64g[lane] : make_double2(0.0, 0.0);
-    const int f64fail = solve_f64(mask, lane, W, Rg, a64, Ldd, cd, ex);
+    const int f64fail = solve_f64<GW>(mask, lane, W, Rg, a64, Ldd, cd, ex);
     if (f64fail) {
         if (row) c[lane] = make_float2(nanf(""), nanf(""));
         if (lane == 0) *info = f64fail;

@@ -313,7 +313,8 @@ __global__ void plain_cov_kernel(const float2 *__restrict__ z, const int64_t *__
                                  float delta, double2 *__restrict__ R) {
     const int64_t g = blockIdx.x;
     const int W = Wg[g], K = Kg[g];
-    const int i = threadIdx.x / 16, j = threadIdx.x % 16;
+    const int side = blockDim.x == 256 ? 16 : 32;   // thread (i, j) per entry
+    const int i = threadIdx.x / side, j = threadIdx.x % side;
     if (i >= W || j >= W) return;
     const float2 *zg = z + ztr_off[g];
     float ar = 0.f, ai = 0.f;
@@ -335,15 +336,18 @@ bs_status launch_window_cov(const bs_plan *p, const void *ztr, const float *delt
     if (p->cfg.flags & BS_FLAG_PLAIN) {
         if (p->cfg.precision != BS_PREC_FP32)
             return set_error(BS_EINVAL, "the plain path is FP32 only");
-        plain_cov_kernel<<<G, 256, 0, st>>>((const float2 *)ztr, p->d_ztr_off, p->d_Wg, p->d_Kg,
-                                            p->d_roff, delta, (float)p->cfg.delta, R);
+        plain_cov_kernel<<<G, p->Wmax <= 16 ? 256 : 1024, 0, st>>>((const float2 *)ztr, p->d_ztr_off, p->d_Wg,
+                                                                   p->d_Kg, p->d_roff, delta, (float)p->cfg.delta, R);
         return check_launch("plain covariance launch");
     }
-    if (p->cfg.precision != BS_PREC_FP32 && !(p->cfg.flags & BS_FLAG_SIMT_COV))
+    // windows above 16 beams: the CTA-per-pair kernel (its 3 x 3 tiles cover
+    // any W; 16-bit windows are widened to FP32 as they are staged)
+    const bool wide = p->Wmax > WMAX_COV;
+    if (wide && p->Wmax > 32) return set_error(BS_EUNSUPPORTED, "W > 32");
+    if (!wide && p->cfg.precision != BS_PREC_FP32 && !(p->cfg.flags & BS_FLAG_SIMT_COV))
         return launch_window_cov_mma(p, ztr, delta, R, st);
     const float inv_sc = 1.0f / p->cfg.store_scale;
-    if (p->Kmax <= 128 && p->pairs >= 4 * (int64_t)p->num_sms) {   // enough pairs to fill the GPU by warps
-        if (p->Wmax > WMAX_COV) return set_error(BS_EUNSUPPORTED, "W > 16");
+    if (!wide && p->Kmax <= 128 && p->pairs >= 4 * (int64_t)p->num_sms) {   // enough pairs to fill the GPU by warps
         const unsigned blocks = (unsigned)((p->pairs + COVW_WARPS - 1) / COVW_WARPS);
         const DF dl = df_from_double(p->cfg.delta);
         switch (p->cfg.precision) {

@@ -63,7 +63,7 @@ def _kw(cfg, u=None, **over):
 
 
 @pytest.mark.parametrize("over,code", [
-    (dict(F=1000), 6), (dict(M=48), 6), (dict(L=3), 1), (dict(W=[17] * 4), 6),
+    (dict(F=1000), 6), (dict(M=48), 6), (dict(L=3), 1), (dict(W=[33] * 4), 6),
     (dict(K=[10 ** 6] * 4), 1), (dict(u=[2.0, 0, 0, 0]), 1), (dict(delta=-1.0), 1),
     (dict(N=128), 6),
 ])

@@ -452,6 +452,57 @@ def test_device_error_word_reaches_caller():
     assert plan.device_status() == 0
 
 
+def wide_config():
+    """Windows above 16 beams (17..32, the whole-warp solve) beside a small
+    one, K below and above W, windows wrapping around beam M - 1."""
+    return scaled_config(all_configs()["C1"], name="wide", N=64, F=256, L=8, M=128, T=6,
+                         W=(17, 32, 24, 25, 5, 20), K=(40, 64, 30, 100, 10, 33), P_tr=7, P_te=2,
+                         n_jam=3, jnr_db=(25.0, 35.0))
+
+
+@pytest.mark.parametrize("precision", [P.BS_PREC_FP32, P.BS_PREC_FP16])
+def test_wide_windows_stages_and_end_to_end(precision):
+    cfg = wide_config()
+    sc = make_scene(cfg)
+    kw = {"store_scale": 2.0} if precision != P.BS_PREC_FP32 else {}
+    res = run_gpu(cfg, sc.x, sc.u_tgt, precision=precision, **kw)
+    if precision == P.BS_PREC_FP32:
+        check_stages(cfg, sc, res)
+    # FP16 windows of streams only about 2W long: the 2^-11 rounding of the
+    # windows, amplified by the conditioning of the loaded covariance, puts
+    # the weights near 1e-3 of the FP64 ones (as on the K = 2W..8W workloads);
+    # the SINR bars stay at 0.1 dB
+    wtol = WEIGHT_TOL if precision == P.BS_PREC_FP32 else 5e-3
+    worst, loss, lref = check_end_to_end(cfg, sc, res, weight_tol=wtol, check_out=precision == P.BS_PREC_FP32)
+    print(f"W up to 32, prec {precision}: max weight rel err {worst:.2e}, max |SINR loss| {loss:.2e} dB "
+          f"(sample R), {lref:.2e} dB (reference R)")
+
+
+@pytest.mark.parametrize("kappa_max,flags", [(1.0001, 0), (0.0, P.BS_FLAG_NO_FP64), (0.0, P.BS_FLAG_NO_REFINE)])
+def test_wide_windows_escalation_paths(kappa_max, flags):
+    """The whole-warp solve's FP64 path (every pair escalated by a tiny
+    kappa_max), its FP32 path without escalation and without refinement:
+    each against the FP64 solve of the GPU's own covariances."""
+    cfg = wide_config()
+    sc = make_scene(cfg)
+    res = run_gpu(cfg, sc.x, sc.u_tgt, flags=flags, kappa_max=kappa_max, keep_xc=False)
+    tol = 1e-4 if flags & P.BS_FLAG_NO_REFINE else SOLVE_TOL
+    for g in range(res.plan.sizes.pairs):
+        pr = res.pair(g)
+        assert pr["info"] == (-2 if kappa_max > 0 else 0), (g, pr["info"])
+        co = O.mvdr_weights(pr["R"], pr["a"])
+        assert rel(pr["c"], co) <= tol, (g, rel(pr["c"], co))
+
+
+def test_wide_windows_plain_path():
+    """The plain FP32 per-pair path (BS_FLAG_PLAIN) with windows up to 32."""
+    cfg = wide_config()
+    sc = make_scene(cfg)
+    res = run_gpu(cfg, sc.x, sc.u_tgt, flags=P.BS_FLAG_PLAIN, keep_xc=False)
+    worst, loss, lref = check_end_to_end(cfg, sc, res, weight_tol=1e-2, check_out=False)
+    print(f"W up to 32, plain FP32: max weight rel err {worst:.2e}")
+
+
 def test_graph_and_autotune():
     """The autotuner picks a launch shape; a captured CUDA graph of the whole
     pass then reproduces bs_run (same shape) bit for bit."""

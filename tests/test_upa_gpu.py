@@ -27,6 +27,11 @@ def _upa_config(kind="paper"):
         # window sizes W_z x W_x: 2 x 4 and 4 x 4 (the paper's), 2 x 2, 3 x 3, 1 x 5
         return scaled_config(all_configs()["C1"], name="upa-4x32", N=128, Nz=4, M=512, Mz=8, T=5,
                              W=(8, 16, 4, 9, 5), Wz=(2, 4, 2, 3, 1), K=64, P_tr=2, P_te=1, n_jam=2)
+    if kind == "wide":
+        # the paper's 4 x 8 window (E2) and other windows above 16 beams:
+        # 4 x 8, 4 x 6, 4 x 4, 2 x 4
+        return scaled_config(all_configs()["C1"], name="upa-4x32-wide", N=128, Nz=4, M=512, Mz=8, T=4,
+                             W=(32, 24, 16, 8), Wz=(4, 4, 4, 2), K=64, P_tr=2, P_te=1, n_jam=2)
     if kind == "large":
         # 4 x 128 elements, 8 x 256 beams: one vector per CTA (its buffers fill the shared memory)
         return scaled_config(all_configs()["C1"], name="upa-4x128", N=512, Nz=4, M=2048, Mz=8, T=3,
@@ -37,6 +42,7 @@ def _upa_config(kind="paper"):
 
 
 @pytest.mark.parametrize("kind,precision", [("paper", P.BS_PREC_FP32), ("paper", P.BS_PREC_FP16),
+                                            ("wide", P.BS_PREC_FP32), ("wide", P.BS_PREC_FP16),
                                             ("large", P.BS_PREC_FP32), ("column", P.BS_PREC_FP32)])
 def test_planar_pipeline_matches_oracle(kind, precision):
     cfg = _upa_config(kind)
