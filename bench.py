@@ -56,7 +56,8 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="time bs_run calls instead of a CUDA graph")
-    ap.add_argument("--autotune", action="store_true", help="autotune the fused kernel before timing")
+    ap.add_argument("--autotune", action="store_true",
+                    help="autotune the pass (kernel variant per stage, fused or not) before timing")
     ap.add_argument("--fused", action="store_true", help="fused persistent covariance + solve kernel")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="budget of the oracle sample timed for cpu_baseline")
@@ -270,13 +271,18 @@ def run_ours(args):
     b.x.copy_(torch.from_numpy(scene.x.reshape(-1)))
     stream = torch.cuda.Stream(dev)
 
+    tune = None
+    if args.autotune:
+        tune = P.bs_autotune_pass(plan, b, stream=stream)
+    fused = args.fused or bool(tune and tune["fused"])
+
     def stages_for(pl, bb):
         return [
             ("channelize", lambda: P.bs_channelize(pl, bb.x, bb.xc, stream=stream)),
             ("beamspace", lambda: P.bs_beamspace(pl, bb.xc, bb.z_train, bb.z_test, stream=stream)),
         ] + ([
             ("cov_solve", lambda: P.bs_cov_solve(pl, bb.z_train, bb.c, bb.info, R=bb.R, stream=stream)),
-        ] if args.fused else [
+        ] if fused else [
             ("window_cov", lambda: P.bs_window_cov(pl, bb.z_train, bb.R, stream=stream)),
             ("mvdr_solve", lambda: P.bs_mvdr_solve(pl, bb.R, bb.c, bb.info, stream=stream)),
         ]) + [
@@ -294,9 +300,6 @@ def run_ours(args):
             ("apply", lambda: P.bs_apply(pl, bb.z_test, bb.c, bb.out, stream=stream)),
         ]
 
-    tune = None
-    if args.autotune:
-        tune = P.bs_autotune(plan, b, stream=stream)
     graph = None if args.no_graph else P.Graph(plan, b, stream)
 
     def step():
@@ -344,8 +347,25 @@ def run_ours(args):
         pbd = stage_breakdown(plain_stages(pplan, pb), max(3, args.steps // 4))
         p_core = pbd["window_cov"] + pbd["mvdr_solve"]
         plain = {"ms_per_step": pms, "value": cfg.pairs / (pms / 1e3),
-                 "solve_core_ms": p_core, "solve_core_pairs_per_s": cfg.pairs / (p_core / 1e3)}
+                 "solve_core_ms": p_core, "solve_core_pairs_per_s": cfg.pairs / (p_core / 1e3),
+                 "path": "one CTA per pair, FP32 sums, one thread per Cholesky, no refinement"}
         del pb, pplan
+    # the tuned FP32 path (FP32 windows through the library's own covariance
+    # and solve kernels) as a second, harder denominator
+    fp32_tuned = None
+    if not args.no_plain and prec != P.BS_PREC_FP32:
+        tplan = P.Plan.from_scene_config(cfg, scene.u_tgt, precision=P.BS_PREC_FP32)
+        tb = P.alloc_buffers(tplan, dev)
+        tb.x.copy_(b.x)
+        P.bs_run(tplan, tb, stream=stream)
+        tbd = stage_breakdown([
+            ("window_cov", lambda: P.bs_window_cov(tplan, tb.z_train, tb.R, stream=stream)),
+            ("mvdr_solve", lambda: P.bs_mvdr_solve(tplan, tb.R, tb.c, tb.info, stream=stream)),
+        ], max(3, args.steps // 4))
+        t_core = tbd["window_cov"] + tbd["mvdr_solve"]
+        fp32_tuned = {"solve_core_ms": t_core, "solve_core_pairs_per_s": cfg.pairs / (t_core / 1e3),
+                      "path": "FP32 windows through the library's FP32 covariance and solve kernels"}
+        del tb, tplan
 
     e2e = None
     if not args.no_e2e:
@@ -380,7 +400,7 @@ def run_ours(args):
     breakdown = stage_breakdown(stages, args.steps)
     other = stage_breakdown([
         ("cov_solve", lambda: P.bs_cov_solve(plan, b.z_train, b.c, b.info, R=b.R, stream=stream)),
-    ] if not args.fused else [
+    ] if not fused else [
         ("window_cov", lambda: P.bs_window_cov(plan, b.z_train, b.R, stream=stream)),
         ("mvdr_solve", lambda: P.bs_mvdr_solve(plan, b.R, b.c, b.info, stream=stream)),
     ], max(3, args.steps // 4))
@@ -442,11 +462,13 @@ def run_ours(args):
     per_stage = {k: {"ms": v, "GB/s": abytes[k] / (v / 1e3) / 1e9,
                      "frac_hbm": abytes[k] / (v / 1e3) / 1e9 / peaks["hbm_gbs"]}
                  for k, v in breakdown.items()}
-    solve_core_ms = (breakdown["cov_solve"] if args.fused
+    solve_core_ms = (breakdown["cov_solve"] if fused
                      else breakdown["window_cov"] + breakdown["mvdr_solve"])
     if plain is not None:
         plain["solve_core_speedup_of_ours"] = plain["solve_core_ms"] / solve_core_ms
         plain["step_speedup_of_ours"] = plain["ms_per_step"] / ms_step
+    if fp32_tuned is not None:
+        fp32_tuned["solve_core_speedup_of_ours"] = fp32_tuned["solve_core_ms"] / solve_core_ms
 
     cpu = None
     accuracy = None
@@ -503,7 +525,7 @@ def run_ours(args):
             "autotune": tune,
             "clocks": clocks, "stages": per_stage, "solve_core_ms": solve_core_ms,
             "other_solve_core_ms": other,
-            "plain_fp32": plain, "accuracy": accuracy, "lifted_correlator": lifted, "range_doppler": radar,
+            "plain_fp32": plain, "fp32_tuned": fp32_tuned, "accuracy": accuracy, "lifted_correlator": lifted, "range_doppler": radar,
             "info_counts": {str(k): int(v) for k, v in zip(*np.unique(info, return_counts=True))},
         }
         print(json.dumps(line), flush=True)

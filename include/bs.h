@@ -288,6 +288,32 @@ bs_status bs_cov_solve(const bs_plan *plan, const void *z_train, const float *de
 bs_status bs_autotune(bs_plan *plan, const void *z_train, bs_cf64 *R, bs_cf32 *c, int32_t *info,
                       bs_stream stream, int32_t *threads, int32_t *ctas_per_sm, float *ms);
 
+/* Choices of bs_autotune_pass (-1 where a stage was not tuned) and the
+ * time of every candidate (ms per launch, < 0 where it does not apply). */
+typedef struct {
+    int32_t beamspace;       /* 0 warp per beam residue, 1 bulk-copy-staged Stockham, 2 one-shot */
+    int32_t covariance;      /* 0 CTA per pair, 1 warp per pair (K <= 128), 2 tensor cores (16-bit windows) */
+    int32_t fused;           /* 1: covariance + solve as one persistent launch (bs_cov_solve) */
+    int32_t ctas_per_sm;     /* of that launch, from bs_autotune */
+    float beamspace_ms[3];
+    float covariance_ms[3];
+    float solve_ms;          /* bs_mvdr_solve after the chosen covariance */
+    float fused_ms;          /* the fused launch at its best shape */
+} bs_tune_report;
+
+/* Autotunes a whole pass on the caller's buffers (buf->x holding a
+ * representative raw cube): channelises once, then times every kernel
+ * variant that applies to the plan for the beamspace stage and for the
+ * covariance (each a different tiling of the same stage: a warp per beam
+ * residue, bulk-copy-staged radix-16 passes or a one-shot CTA per group;
+ * a CTA, a warp or tensor-core fragments per pair), the fused covariance +
+ * solve at every CTAs-per-SM shape (bs_autotune) against the two launches,
+ * and keeps the fastest of each in the plan; bs_run, bs_run_host and
+ * bs_graph_create use them from then on.  Results of the chosen variants
+ * meet the same tolerances (their sums round differently).  Synchronises
+ * `stream`; overwrites xc, the windows, R, c and info.  rep may be NULL. */
+bs_status bs_autotune_pass(bs_plan *plan, const bs_buffers *buf, bs_stream stream, bs_tune_report *rep);
+
 /* Sets the launch shape of bs_cov_solve (threads 128; 1..32 CTAs per SM). */
 bs_status bs_set_launch(bs_plan *plan, int32_t threads, int32_t ctas_per_sm);
 

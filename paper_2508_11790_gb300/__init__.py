@@ -21,7 +21,7 @@ __all__ = [
     "BS_PREC_FP32", "BS_PREC_FP16", "BS_PREC_BF16",
     "BS_FLAG_PLAIN", "BS_FLAG_NO_REFINE", "BS_FLAG_NO_FP64", "BS_FLAG_NO_TMA", "BS_FLAG_FUSED", "BS_FLAG_SIMT_COV",
     "BS_FLAG_STAGED_FFT",
-    "bs_cov_solve", "bs_autotune", "bs_set_launch", "Graph", "bs_cov_solve_noalloc",
+    "bs_cov_solve", "bs_autotune", "bs_autotune_pass", "bs_set_launch", "Graph", "bs_cov_solve_noalloc",
     "BsError", "Plan", "Buffers", "alloc_buffers", "lib", "bs_plan_tables_host",
     "bs_channelize", "bs_beamspace", "bs_beamspace_full", "bs_window_cov",
     "bs_mvdr_solve", "bs_mvdr_solve_precond", "bs_apply", "bs_run", "bs_run_host",
@@ -97,6 +97,7 @@ _SIGS = {
     "bs_cov_solve": ([_P, _P, _P, _P, _P, _P, _P], ctypes.c_int),
     "bs_autotune": ([_P, _P, _P, _P, _P, _P, _P, _P, _P], ctypes.c_int),
     "bs_set_launch": ([_P, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
+    "bs_autotune_pass": ([_P, ctypes.POINTER(_Buffers), _P, _P], ctypes.c_int),
     "bs_cov_solve_noalloc": ([_P, ctypes.c_int32, ctypes.c_float, _P, _P, _P, _P, _P, _P, _P, ctypes.c_int64,
                               ctypes.c_double, ctypes.c_double, ctypes.c_uint32, _P, _P, _P], ctypes.c_int),
     "bs_graph_create": ([_P, ctypes.POINTER(_Buffers), _P, ctypes.POINTER(_P)], ctypes.c_int),
@@ -420,6 +421,37 @@ def bs_autotune(plan: Plan, bufs: "Buffers", stream=None) -> dict:
                              _ptr(bufs.info, torch.int32, s.pairs, "info"), _stream(stream),
                              ctypes.byref(thr), ctypes.byref(cps), ctypes.byref(ms)), "bs_autotune")
     return {"threads": thr.value, "ctas_per_sm": cps.value, "ms": ms.value}
+
+
+class _TuneReport(ctypes.Structure):
+    _fields_ = [("beamspace", ctypes.c_int32), ("covariance", ctypes.c_int32), ("fused", ctypes.c_int32),
+                ("ctas_per_sm", ctypes.c_int32), ("beamspace_ms", ctypes.c_float * 3),
+                ("covariance_ms", ctypes.c_float * 3), ("solve_ms", ctypes.c_float), ("fused_ms", ctypes.c_float)]
+
+
+BEAMSPACE_VARIANTS = ("warp per beam residue", "bulk-copy-staged radix-16", "one-shot CTA per group")
+COVARIANCE_VARIANTS = ("CTA per pair", "warp per pair", "tensor cores")
+
+
+def bs_autotune_pass(plan: Plan, bufs: "Buffers", stream=None) -> dict:
+    """Time every kernel variant of the beamspace and covariance stages and
+    the fused covariance + solve on these buffers (bufs.x holds the raw
+    cube); the fastest of each is kept in the plan.  Returns the choices and
+    the candidate times (ms, None where a variant does not apply)."""
+    r = _TuneReport()
+    _check(lib().bs_autotune_pass(plan.handle, ctypes.byref(_cbuf(plan, bufs)), _stream(stream), ctypes.byref(r)),
+           "bs_autotune_pass")
+
+    def ms(v):
+        return None if v < 0 else float(v)
+    return {
+        "beamspace": BEAMSPACE_VARIANTS[r.beamspace] if r.beamspace >= 0 else None,
+        "covariance": COVARIANCE_VARIANTS[r.covariance] if r.covariance >= 0 else None,
+        "fused": bool(r.fused), "ctas_per_sm": r.ctas_per_sm,
+        "beamspace_ms": {BEAMSPACE_VARIANTS[k]: ms(r.beamspace_ms[k]) for k in range(3)},
+        "covariance_ms": {COVARIANCE_VARIANTS[k]: ms(r.covariance_ms[k]) for k in range(3)},
+        "solve_ms": ms(r.solve_ms), "fused_ms": ms(r.fused_ms),
+    }
 
 
 def bs_set_launch(plan: Plan, threads: int, ctas_per_sm: int):

@@ -16,6 +16,12 @@ static bs_status check_device(const bs_plan *p) {
     return BS_OK;
 }
 
+// Covariance and solve as one persistent launch: the plan flag, unless
+// bs_autotune_pass has chosen.
+static bool use_fused(const bs_plan *p) {
+    return p->tune_fused >= 0 ? p->tune_fused == 1 : (p->cfg.flags & BS_FLAG_FUSED) != 0;
+}
+
 #define BS_REQUIRE(cond, msg)                                  \
     do {                                                       \
         if (!(cond)) return set_error(BS_EINVAL, (msg));       \
@@ -149,7 +155,7 @@ bs_status bs_run(const bs_plan *p, const bs_buffers *b, bs_stream stream) {
     bs_status s;
     if ((s = bs_channelize(p, b->x, p->P, b->xc, stream))) return s;
     if ((s = bs_beamspace(p, b->xc, b->z_train, b->z_test, stream))) return s;
-    if (p->cfg.flags & BS_FLAG_FUSED) {
+    if (use_fused(p)) {
         if ((s = bs_cov_solve(p, b->z_train, nullptr, b->R, b->c, b->info, stream))) return s;
     } else {
         if ((s = bs_window_cov(p, b->z_train, nullptr, b->R, stream))) return s;
@@ -248,6 +254,99 @@ bs_status bs_autotune(bs_plan *p, const void *z_train, bs_cf64 *R, bs_cf32 *c, i
     return BS_OK;
 }
 
+bs_status bs_autotune_pass(bs_plan *p, const bs_buffers *b, bs_stream stream, bs_tune_report *rep) {
+    BS_REQUIRE(p && b, "NULL argument");
+    BS_REQUIRE(b->x && b->xc && b->z_train && b->R && b->c && b->info, "buf->x, xc, z_train, R, c, info needed");
+    if (bs_status s = check_device(p)) return s;
+    const cudaStream_t st = (cudaStream_t)stream;
+    bs_tune_report r;
+    for (int k = 0; k < 3; ++k) r.beamspace_ms[k] = r.covariance_ms[k] = -1.f;
+    r.solve_ms = r.fused_ms = -1.f;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return bs::cuda_error(cudaGetLastError(), "event create");
+    // mean time of `reps` runs after one warm-up run; < 0 if it failed
+    auto time_of = [&](auto &&run, float *ms) -> bs_status {
+        bs_status s = run();
+        if (s) return s;
+        cudaEventRecord(e0, st);
+        constexpr int reps = 3;
+        for (int k = 0; k < reps && !s; ++k) s = run();
+        cudaEventRecord(e1, st);
+        if (s) return s;
+        cudaError_t e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) return bs::cuda_error(e, "autotune");
+        cudaEventElapsedTime(ms, e0, e1);
+        *ms /= reps;
+        return BS_OK;
+    };
+    const int saved_b = p->tune_beamspace, saved_c = p->tune_cov, saved_f = p->tune_fused;
+    bs_status s = bs::launch_channelize(p, (const float2 *)b->x, p->P, (float2 *)b->xc, st);
+    // beamspace: the variants that apply to this plan
+    int best_b = -1;
+    float best = 1e30f;
+    if (!s && !p->planar) {
+        for (int v = 0; v < 3 && !s; ++v) {
+            const bool applies = (v == 0) ? (p->cfg.M == 1024 || p->cfg.M == 2048 || p->cfg.M == 4096) &&
+                                                p->cfg.N <= 1024 && p->cfg.T <= 256 && !(p->cfg.flags & BS_FLAG_NO_TMA)
+                                 : (v == 1) ? p->cfg.M >= 512 && !(p->cfg.N & 1) && !(p->cfg.flags & BS_FLAG_NO_TMA) &&
+                                                  (p->Fs % p->vpb) == 0 && (p->B % p->vpb) == 0
+                                            : true;
+            if (!applies) continue;
+            p->tune_beamspace = v;
+            float ms = 0.f;
+            s = time_of([&] { return bs::launch_beamspace(p, (const float2 *)b->xc, b->z_train, (float2 *)b->z_test, st); },
+                        &ms);
+            r.beamspace_ms[v] = ms;
+            if (!s && ms < best) best = ms, best_b = v;
+        }
+    }
+    p->tune_beamspace = best_b;
+    if (!s) s = bs::launch_beamspace(p, (const float2 *)b->xc, b->z_train, (float2 *)b->z_test, st);
+    // covariance
+    int best_c = -1;
+    best = 1e30f;
+    const bool narrow = p->Wmax <= 16;
+    for (int v = 0; v < 3 && !s; ++v) {
+        const bool applies = (v == 0) || (v == 1 && narrow && p->Kmax <= 128) ||
+                             (v == 2 && narrow && p->cfg.precision != BS_PREC_FP32);
+        if (!applies || (p->cfg.flags & BS_FLAG_PLAIN)) continue;
+        p->tune_cov = v;
+        float ms = 0.f;
+        s = time_of([&] { return bs::launch_window_cov(p, b->z_train, nullptr, (double2 *)b->R, st); }, &ms);
+        r.covariance_ms[v] = ms;
+        if (!s && ms < best) best = ms, best_c = v;
+    }
+    p->tune_cov = best_c;
+    if (!s) s = bs::launch_window_cov(p, b->z_train, nullptr, (double2 *)b->R, st);
+    if (!s) s = time_of([&] { return bs::launch_mvdr_solve(p, (const double2 *)b->R, (float2 *)b->c, b->info, st); },
+                        &r.solve_ms);
+    // the fused persistent kernel (W <= 16) at its best CTAs per SM, against the two launches
+    int best_f = 0;
+    if (!s && narrow && !(p->cfg.flags & BS_FLAG_PLAIN)) {
+        int32_t thr = 0, cps = 0;
+        float fms = 0.f;
+        s = bs_autotune(p, b->z_train, b->R, b->c, b->info, stream, &thr, &cps, &fms);
+        r.fused_ms = fms;
+        if (!s && fms < best + r.solve_ms) best_f = 1;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s) {
+        p->tune_beamspace = saved_b;
+        p->tune_cov = saved_c;
+        p->tune_fused = saved_f;
+        return s;
+    }
+    p->tune_fused = best_f;
+    r.beamspace = best_b;
+    r.covariance = best_c;
+    r.fused = best_f;
+    r.ctas_per_sm = p->cs.ctas_per_sm;
+    if (rep) *rep = r;
+    return BS_OK;
+}
+
 bs_status bs_set_launch(bs_plan *p, int32_t threads, int32_t ctas_per_sm) {
     BS_REQUIRE(p, "NULL plan");
     BS_REQUIRE(threads == 128, "threads must be 128");
@@ -296,7 +395,7 @@ bs_status bs_run_host(const bs_plan *p, const bs_cf32 *x_host, bs_cf32 *out_host
         if ((s = bs::launch_beamspace(p, (const float2 *)b->xc, b->z_train, (float2 *)b->z_test, st, p0, np)))
             return s;
         if (bounds[k + 1] == Ptr) {   // every training window is in place
-            if (p->cfg.flags & BS_FLAG_FUSED) {
+            if (use_fused(p)) {
                 if ((s = bs_cov_solve(p, b->z_train, nullptr, b->R, b->c, b->info, stream))) return s;
             } else {
                 if ((s = bs_window_cov(p, b->z_train, nullptr, b->R, stream))) return s;

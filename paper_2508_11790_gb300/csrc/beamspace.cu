@@ -196,10 +196,16 @@ bs_status launch_beamspace(const bs_plan *p, const float2 *xc, void *ztr, float2
     ga.store_scale = p->cfg.store_scale;
     if (p->planar) return launch_beamspace2d(p, xc, ga, st);
     bool used = false;
-    bs_status s = launch_beamspace_warp(p, xc, ga, st, &used);
-    if (s || used) return s;
-    s = launch_beamspace_tma(p, xc, ga, st, &used);
-    if (s || used) return s;
+    bs_status s = BS_OK;
+    const int v = p->tune_beamspace;   // -1: the first variant that applies, in this order
+    if (v <= 0) {
+        s = launch_beamspace_warp(p, xc, ga, st, &used);
+        if (s || used) return s;
+    }
+    if (v <= 1) {
+        s = launch_beamspace_tma(p, xc, ga, st, &used);
+        if (s || used) return s;
+    }
     switch (p->cfg.precision) {
         case BS_PREC_FP32: return launch_bs<false, BS_PREC_FP32>(p->cfg.M, xc, ga.nvec, p->cfg.N, p->d_twM, nullptr, ga, st);
         case BS_PREC_FP16: return launch_bs<false, BS_PREC_FP16>(p->cfg.M, xc, ga.nvec, p->cfg.N, p->d_twM, nullptr, ga, st);

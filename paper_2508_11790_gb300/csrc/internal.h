@@ -69,6 +69,10 @@ struct bs_plan {
     int64_t nsmall = 0;   // pairs with W <= 16 (the first of order_w)
     int *d_head = nullptr;
     bs::CovSolveLaunch cs;
+    // kernel variants chosen by bs_autotune_pass (-1: the built-in choice)
+    int tune_beamspace = -1;   // 0 warp per residue, 1 bulk-copy staged, 2 one-shot
+    int tune_cov = -1;         // 0 CTA per pair, 1 warp per pair, 2 tensor cores
+    int tune_fused = -1;       // 0 covariance + solve as two launches, 1 one persistent launch
 };
 
 namespace bs {

@@ -344,10 +344,14 @@ bs_status launch_window_cov(const bs_plan *p, const void *ztr, const float *delt
     // any W; 16-bit windows are widened to FP32 as they are staged)
     const bool wide = p->Wmax > WMAX_COV;
     if (wide && p->Wmax > 32) return set_error(BS_EUNSUPPORTED, "W > 32");
-    if (!wide && p->cfg.precision != BS_PREC_FP32 && !(p->cfg.flags & BS_FLAG_SIMT_COV))
+    const int tv = p->tune_cov;   // a variant chosen by bs_autotune_pass, where it applies
+    const bool mma_ok = !wide && p->cfg.precision != BS_PREC_FP32;
+    const bool warp_ok = !wide && p->Kmax <= 128;
+    if (mma_ok && (tv == 2 || (tv < 0 && !(p->cfg.flags & BS_FLAG_SIMT_COV))))
         return launch_window_cov_mma(p, ztr, delta, R, st);
     const float inv_sc = 1.0f / p->cfg.store_scale;
-    if (!wide && p->Kmax <= 128 && p->pairs >= 4 * (int64_t)p->num_sms) {   // enough pairs to fill the GPU by warps
+    // warp per pair: short streams over enough pairs to fill the GPU by warps
+    if (warp_ok && (tv == 1 || (tv < 0 && p->pairs >= 4 * (int64_t)p->num_sms))) {
         const unsigned blocks = (unsigned)((p->pairs + COVW_WARPS - 1) / COVW_WARPS);
         const DF dl = df_from_double(p->cfg.delta);
         switch (p->cfg.precision) {

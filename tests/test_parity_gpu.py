@@ -24,7 +24,7 @@ import torch
 import oracle as O
 import paper_2508_11790_gb300 as P
 from synth import all_configs, make_scene, reference_records, scaled_config
-from gpu_helpers import rel, run_gpu
+from gpu_helpers import GpuResult, rel, run_gpu, ztrain_to_complex
 
 pytestmark = pytest.mark.gpu
 
@@ -501,6 +501,39 @@ def test_wide_windows_plain_path():
     res = run_gpu(cfg, sc.x, sc.u_tgt, flags=P.BS_FLAG_PLAIN, keep_xc=False)
     worst, loss, lref = check_end_to_end(cfg, sc, res, weight_tol=1e-2, check_out=False)
     print(f"W up to 32, plain FP32: max weight rel err {worst:.2e}")
+
+
+@pytest.mark.parametrize("precision", [P.BS_PREC_FP32, P.BS_PREC_FP16])
+def test_pass_autotuner(precision):
+    """bs_autotune_pass times every beamspace and covariance variant that
+    applies and the fused launch, keeps the fastest, and the tuned pass (and
+    its CUDA graph) still meets the oracle's tolerances."""
+    cfg = scaled_config(uneven_small_config(), name="tune", M=1024, N=256, F=512, L=16)
+    sc = make_scene(cfg)
+    kw = {"store_scale": 2.0} if precision != P.BS_PREC_FP32 else {}
+    plan = P.Plan.from_scene_config(cfg, sc.u_tgt, precision=precision, **kw)
+    b = P.alloc_buffers(plan)
+    b.x.copy_(torch.from_numpy(sc.x.reshape(-1)))
+    st = torch.cuda.Stream()
+    rep = P.bs_autotune_pass(plan, b, stream=st)
+    bms, cms = rep["beamspace_ms"], rep["covariance_ms"]
+    assert all(v is not None and v > 0 for v in bms.values())          # M = 1024: all three apply
+    assert cms["CTA per pair"] > 0 and cms["warp per pair"] > 0         # K <= 128
+    assert (cms["tensor cores"] is not None) == (precision != P.BS_PREC_FP32)
+    assert rep["beamspace"] == min((v, k) for k, v in bms.items())[1]
+    assert rep["covariance"] == min((v, k) for k, v in cms.items() if v is not None)[1]
+    assert rep["solve_ms"] > 0 and rep["fused_ms"] > 0
+    g = P.Graph(plan, b, st)
+    g.launch(st)
+    st.synchronize()
+    res = GpuResult(plan=plan, off=plan.offsets(), xc=None,
+                    z_train=ztrain_to_complex(plan, b.z_train, kw.get("store_scale", 1.0)),
+                    z_test=b.z_test.cpu().numpy(), R=b.R.cpu().numpy(), c=b.c.cpu().numpy(),
+                    info=b.info.cpu().numpy(),
+                    out=b.out.cpu().numpy()[: plan.sizes.out_elems].reshape(plan.sizes.pairs, -1))
+    wtol = WEIGHT_TOL if precision == P.BS_PREC_FP32 else 5e-3
+    check_end_to_end(cfg, sc, res, weight_tol=wtol, check_out=precision == P.BS_PREC_FP32)
+    assert plan.device_status() == 0
 
 
 def test_graph_and_autotune():
