@@ -13,7 +13,7 @@ namespace bs {
 
 constexpr int SOLVE_PAIRS_PER_CTA = 8;
 
-__global__ void __launch_bounds__(SOLVE_PAIRS_PER_CTA * 16, 5)
+__global__ void __launch_bounds__(SOLVE_PAIRS_PER_CTA * 16, 4)
     mvdr_solve_kernel(const double2 *__restrict__ R, const int64_t *__restrict__ roff,
                       const int32_t *__restrict__ Wg, const int64_t *__restrict__ woff,
                       const float2 *__restrict__ at32, const float2 *__restrict__ atlo,
@@ -28,8 +28,8 @@ __global__ void __launch_bounds__(SOLVE_PAIRS_PER_CTA * 16, 5)
     if (slot >= pairs) return;   // uniform over the half-warp
     const int64_t g = order ? (int64_t)order[slot] : slot;   // pairs grouped by W
     const int64_t wo = woff[g];
-    solve_pair(mask, lane, Wg[g], R + roff[g], at32 + wo, atlo + wo, at64 + wo, c + wo, info + g, kappa_max, refine,
-               allow_f64, scratch[hw], dpre ? dpre + wo : nullptr);
+    solve_pair_inline(mask, lane, Wg[g], R + roff[g], at32 + wo, atlo + wo, at64 + wo, c + wo, info + g, kappa_max,
+                      refine, allow_f64, scratch[hw], dpre ? dpre + wo : nullptr);
 }
 
 // Windows of 17..32 beams: one warp per pair, solved at WT = 24 or 32 with

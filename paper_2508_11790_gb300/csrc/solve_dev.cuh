@@ -276,7 +276,7 @@ __device__ __forceinline__ float2 split_f64(double d) {
 // double2 per half-warp.  Writes c[0..W) and *info.  Not inlined, so each
 // window size is compiled once per translation unit.
 template <int WT, int GW = 16>
-static __device__ __noinline__ void solve_pair_fixed(unsigned mask, int lane, const double2 *Rg,
+__device__ __forceinline__ void solve_pair_body(unsigned mask, int lane, const double2 *Rg,
                                                      const float2 *__restrict__ a32g,
                                                      const float2 *__restrict__ alog,
                                                      const double2 *__restrict__ a64g, float2 *__restrict__ c,
@@ -384,6 +384,41 @@ static __device__ __noinline__ void solve_pair_fixed(unsigned mask, int lane, co
     }
     if (row) c[lane] = make_float2((float)cd.x, (float)cd.y);
     if (lane == 0) *info = -2;
+}
+
+// The same solve as a separate function per window size (the fused and
+// whole-warp kernels call it: one copy of the body per W and translation
+// unit, and their own registers stay free of it).
+template <int WT, int GW = 16>
+static __device__ __noinline__ void solve_pair_fixed(unsigned mask, int lane, const double2 *Rg,
+                                                     const float2 *__restrict__ a32g,
+                                                     const float2 *__restrict__ alog,
+                                                     const double2 *__restrict__ a64g, float2 *__restrict__ c,
+                                                     int32_t *__restrict__ info, double kappa_max, int refine,
+                                                     int allow_f64, double2 (*scratch)[GW + 1],
+                                                     const float *__restrict__ dg) {
+    solve_pair_body<WT, GW>(mask, lane, Rg, a32g, alog, a64g, c, info, kappa_max, refine, allow_f64, scratch, dg);
+}
+
+// The solve of every window size inlined into the calling kernel (the
+// stand-alone solve: its pairs are grouped by W, so the warps resident on
+// an SM run one body; with calls instead, every call saved and restored
+// the caller's live registers in local memory).
+__device__ __forceinline__ void solve_pair_inline(unsigned mask, int lane, int W, const double2 *Rg,
+                                                  const float2 *__restrict__ a32g, const float2 *__restrict__ alog,
+                                                  const double2 *__restrict__ a64g, float2 *__restrict__ c,
+                                                  int32_t *__restrict__ info, double kappa_max, int refine,
+                                                  int allow_f64, double2 (*scratch)[WMAX + 1],
+                                                  const float *__restrict__ dg) {
+#define BS_SOLVE_CASE(n) \
+    case n: solve_pair_body<n>(mask, lane, Rg, a32g, alog, a64g, c, info, kappa_max, refine, allow_f64, scratch, dg); break;
+    switch (W) {
+        BS_SOLVE_CASE(1) BS_SOLVE_CASE(2) BS_SOLVE_CASE(3) BS_SOLVE_CASE(4)
+        BS_SOLVE_CASE(5) BS_SOLVE_CASE(6) BS_SOLVE_CASE(7) BS_SOLVE_CASE(8)
+        BS_SOLVE_CASE(9) BS_SOLVE_CASE(10) BS_SOLVE_CASE(11) BS_SOLVE_CASE(12)
+        BS_SOLVE_CASE(13) BS_SOLVE_CASE(14) BS_SOLVE_CASE(15) default: BS_SOLVE_CASE(16)
+    }
+#undef BS_SOLVE_CASE
 }
 
 // R stored as FP64 (global or shared memory); dispatches on W to the solve
