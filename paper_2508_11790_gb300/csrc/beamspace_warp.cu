@@ -38,6 +38,10 @@ namespace {
 
 constexpr int kRow = 33;                // padded row of the 32 x 32 transpose
 constexpr int kBuf = 32 * kRow;         // float2 per warp
+// Distance between the buffers of one vector's residues: 8 float2 (16
+// banks) more than a buffer, so that the gather's reads of beams 2k and
+// 2k + 1 (residues 0 and 1 at the same offset) fall in different banks.
+constexpr int kBufS = kBuf + 8;
 constexpr int kWarpGatherRegs = 12;     // gather entries per lane held in registers
 constexpr int kBatch = 4;               // gather entries whose loads are issued together
 
@@ -153,9 +157,13 @@ __device__ __forceinline__ void warp_units(const WarpArgs &wa, const GatherArgs 
     constexpr int M = 1024 * R;
     constexpr int log2r = (R == 1) ? 0 : (R == 2 ? 1 : 2);
     const int lane = threadIdx.x & 31;
-    float2 *buf = grp + CC * kBuf;
+    float2 *buf = grp + CC * kBufS;
     const float2 *twc = tw + CC * 1024;
     const float2 *ptc = ptw + CC * 32;
+    // the inter-stage twiddles of this lane, W_M^(n2 (R k1 + CC)), are a
+    // geometric sequence in k1 with ratio rho = W_M^(n2 R): read every 8th
+    // from the table and step 7 times by rho (at most 7 roundings)
+    const float2 rho0 = tw[32 + lane];   // W_M^(n2 R) (the table's residue-0 row k1 = 1)
     float2 a[32];
     auto load = [&](int64_t v) {   // column n2 = lane of vector v
         const float2 *src = wa.y + v * wa.N + lane;
@@ -177,13 +185,25 @@ __device__ __forceinline__ void warp_units(const WarpArgs &wa, const GatherArgs 
     if (vec < ga.nvec) load(vec);
     for (; vec < ga.nvec; vec += vstride) {
         // pass 1: residue CC of a (32 R)-point DFT along n1, then the twiddles
-        if (R > 1 && CC != 0) {   // W_(32 R)^(CC n1): one broadcast table row
+        if constexpr (R == 2) {   // W_64^(n1) for residue 1: compile-time constants
+            if (CC == 1) {
+#pragma unroll
+                for (int n1 = 1; n1 < 32; ++n1) a[n1] = twiddle_d<64>(n1, a[n1]);
+            }
+        } else if (R > 1 && CC != 0) {   // W_(32 R)^(CC n1): one broadcast table row
 #pragma unroll
             for (int n1 = 1; n1 < 32; ++n1) a[n1] = cmul(a[n1], ptc[n1]);
         }
         dft32(a);
 #pragma unroll
-        for (int k1 = 0; k1 < 32; ++k1) buf[k1 * kRow + lane] = cmul(a[k1], twc[k1 * 32 + lane]);
+        for (int k8 = 0; k8 < 32; k8 += 8) {
+            float2 t = twc[k8 * 32 + lane];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                if (i) t = cmul(t, rho0);
+                buf[(k8 + i) * kRow + lane] = cmul(a[k8 + i], t);
+            }
+        }
         // this vector's per-target entries, split over the R warps
         const int64_t v = ga.vbase + vec;
         const int p = (int)(v >> ga.log2F);
@@ -227,7 +247,7 @@ __device__ __forceinline__ void warp_units(const WarpArgs &wa, const GatherArgs 
                 const int kk = m >> log2r;
                 // entries that store nothing (training vectors past the
                 // target's K) skip the shared-memory read
-                val[j] = ok[j] ? grp[(m & (R - 1)) * kBuf + (kk & 31) * kRow + (kk >> 5)] : make_float2(0.f, 0.f);
+                val[j] = ok[j] ? grp[(m & (R - 1)) * kBufS + (kk & 31) * kRow + (kk >> 5)] : make_float2(0.f, 0.f);
                 gi[j] = te.base + w;
             }
 #pragma unroll
@@ -256,8 +276,8 @@ __global__ void __launch_bounds__(256, 2)
     extern __shared__ __align__(16) unsigned char smraw[];
     float2 *tw = reinterpret_cast<float2 *>(smraw);    // [R][32 k1][32 n2]
     float2 *ptw = tw + R * 1024;                       // [R][32 n1]
-    float2 *bufs = ptw + R * 32;                       // [8 warps][32][kRow]
-    GatherEnt *tabs = reinterpret_cast<GatherEnt *>(bufs + 8 * kBuf);   // [vpc][T]
+    float2 *bufs = ptw + R * 32;                       // [8 warps][kBufS]
+    GatherEnt *tabs = reinterpret_cast<GatherEnt *>(bufs + 8 * kBufS);   // [vpc][T]
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int slot = warp / R, cc = warp % R;
     for (int e = tid; e < R * 1024; e += 256) {
@@ -272,7 +292,7 @@ __global__ void __launch_bounds__(256, 2)
         gent[j] = (e < wa.sumW) ? __ldg(&wa.glist[e]) : -1;
     }
     __syncthreads();
-    float2 *grp = bufs + slot * R * kBuf;
+    float2 *grp = bufs + slot * R * kBufS;
     GatherEnt *tab = tabs + slot * ga.T;
     const int64_t vec = (int64_t)blockIdx.x * vpc + slot;
     const int64_t vstride = (int64_t)gridDim.x * vpc;
@@ -282,7 +302,7 @@ __global__ void __launch_bounds__(256, 2)
 template <int R, bool kFull, int PREC>
 bs_status launch_warp_t(const bs_plan *p, const float2 *xc, const GatherArgs &ga, cudaStream_t st) {
     constexpr int vpc = 8 / R;
-    const size_t fixed = (size_t)R * 1056 * sizeof(float2) + 8 * (size_t)kBuf * sizeof(float2);
+    const size_t fixed = (size_t)R * 1056 * sizeof(float2) + 8 * (size_t)kBufS * sizeof(float2);
     const size_t smem = fixed + (size_t)vpc * ga.T * sizeof(GatherEnt);
     const size_t smem_max = fixed + (size_t)vpc * kTabT * sizeof(GatherEnt);
     static PerDevice occ;
