@@ -177,6 +177,8 @@ def main(argv=None) -> list:
     ap.add_argument("--detect", action="store_true", help="detection sweep on a coherent pulse-train scene")
     ap.add_argument("--planar", action="store_true", help="the paper's 4 x 32 planar array (with --detect)")
     ap.add_argument("--snr", type=float, default=-20.0, help="per-element target SNR, dB (with --detect)")
+    ap.add_argument("--targets", type=int, default=8, help="targets of the detection scene")
+    ap.add_argument("--jammers", type=int, default=6, help="jammers of the detection scene (40-60 dB JNR)")
     a = ap.parse_args(argv)
     if a.detect:
         return _detect_main(a)
@@ -212,7 +214,7 @@ def _detect_main(a) -> list:
     import json
 
     from synth import pulse
-    cfg, sc = detection_scene(a.config, a.planar, a.snr)
+    cfg, sc = detection_scene(a.config, a.planar, a.snr, T=a.targets, n_jam=a.jammers)
     ps = np.fft.fft(pulse(cfg.F), norm="ortho")   # the transmitted pulse's spectrum: an input of range processing
 
     def pairs(text):
