@@ -78,6 +78,8 @@ typedef enum {
 #define BS_FLAG_SIMT_COV   (1u << 5) /* 16-bit windows: FP32 SIMT products instead of the tensor cores */
 #define BS_FLAG_STAGED_FFT (1u << 6) /* beamspace at M = 1024..4096, N <= 1024: the bulk-copy-staged
                                         Stockham kernel instead of the warp-per-transform kernel */
+#define BS_FLAG_SIMT_FFT   (1u << 7) /* beamspace at N = 1024, M = 2048: the CUDA-core kernels instead
+                                        of the tensor-core DFT */
 
 typedef struct { float re, im; } bs_cf32;
 typedef struct { double re, im; } bs_cf64;
@@ -291,11 +293,12 @@ bs_status bs_autotune(bs_plan *plan, const void *z_train, bs_cf64 *R, bs_cf32 *c
 /* Choices of bs_autotune_pass (-1 where a stage was not tuned) and the
  * time of every candidate (ms per launch, < 0 where it does not apply). */
 typedef struct {
-    int32_t beamspace;       /* 0 warp per beam residue, 1 bulk-copy-staged Stockham, 2 one-shot */
+    int32_t beamspace;       /* 0 warp per beam residue, 1 bulk-copy-staged Stockham, 2 one-shot,
+                                3 tensor-core DFT (N = 1024, M = 2048) */
     int32_t covariance;      /* 0 CTA per pair, 1 warp per pair (K <= 128), 2 tensor cores (16-bit windows) */
     int32_t fused;           /* 1: covariance + solve as one persistent launch (bs_cov_solve) */
     int32_t ctas_per_sm;     /* of that launch, from bs_autotune */
-    float beamspace_ms[3];
+    float beamspace_ms[4];
     float covariance_ms[3];
     float solve_ms;          /* bs_mvdr_solve after the chosen covariance */
     float fused_ms;          /* the fused launch at its best shape */
@@ -305,7 +308,8 @@ typedef struct {
  * representative raw cube): channelises once, then times every kernel
  * variant that applies to the plan for the beamspace stage and for the
  * covariance (each a different tiling of the same stage: a warp per beam
- * residue, bulk-copy-staged radix-16 passes or a one-shot CTA per group;
+ * residue, bulk-copy-staged radix-16 passes, a one-shot CTA per group or
+ * the tensor-core DFT;
  * a CTA, a warp or tensor-core fragments per pair), the fused covariance +
  * solve at every CTAs-per-SM shape (bs_autotune) against the two launches,
  * and keeps the fastest of each in the plan; bs_run, bs_run_host and

@@ -20,7 +20,7 @@ from .build import lib_path
 __all__ = [
     "BS_PREC_FP32", "BS_PREC_FP16", "BS_PREC_BF16",
     "BS_FLAG_PLAIN", "BS_FLAG_NO_REFINE", "BS_FLAG_NO_FP64", "BS_FLAG_NO_TMA", "BS_FLAG_FUSED", "BS_FLAG_SIMT_COV",
-    "BS_FLAG_STAGED_FFT",
+    "BS_FLAG_STAGED_FFT", "BS_FLAG_SIMT_FFT",
     "bs_cov_solve", "bs_autotune", "bs_autotune_pass", "bs_set_launch", "Graph", "bs_cov_solve_noalloc",
     "BsError", "Plan", "Buffers", "alloc_buffers", "lib", "bs_plan_tables_host",
     "bs_channelize", "bs_beamspace", "bs_beamspace_full", "bs_window_cov",
@@ -32,6 +32,7 @@ BS_PREC_FP32, BS_PREC_FP16, BS_PREC_BF16 = 0, 1, 2
 BS_FLAG_PLAIN, BS_FLAG_NO_REFINE, BS_FLAG_NO_FP64, BS_FLAG_NO_TMA, BS_FLAG_FUSED = 1, 2, 4, 8, 16
 BS_FLAG_SIMT_COV = 32
 BS_FLAG_STAGED_FFT = 64
+BS_FLAG_SIMT_FFT = 128
 
 
 class BsError(RuntimeError):
@@ -425,11 +426,12 @@ def bs_autotune(plan: Plan, bufs: "Buffers", stream=None) -> dict:
 
 class _TuneReport(ctypes.Structure):
     _fields_ = [("beamspace", ctypes.c_int32), ("covariance", ctypes.c_int32), ("fused", ctypes.c_int32),
-                ("ctas_per_sm", ctypes.c_int32), ("beamspace_ms", ctypes.c_float * 3),
+                ("ctas_per_sm", ctypes.c_int32), ("beamspace_ms", ctypes.c_float * 4),
                 ("covariance_ms", ctypes.c_float * 3), ("solve_ms", ctypes.c_float), ("fused_ms", ctypes.c_float)]
 
 
-BEAMSPACE_VARIANTS = ("warp per beam residue", "bulk-copy-staged radix-16", "one-shot CTA per group")
+BEAMSPACE_VARIANTS = ("warp per beam residue", "bulk-copy-staged radix-16", "one-shot CTA per group",
+                      "tensor-core DFT")
 COVARIANCE_VARIANTS = ("CTA per pair", "warp per pair", "tensor cores")
 
 
@@ -448,7 +450,7 @@ def bs_autotune_pass(plan: Plan, bufs: "Buffers", stream=None) -> dict:
         "beamspace": BEAMSPACE_VARIANTS[r.beamspace] if r.beamspace >= 0 else None,
         "covariance": COVARIANCE_VARIANTS[r.covariance] if r.covariance >= 0 else None,
         "fused": bool(r.fused), "ctas_per_sm": r.ctas_per_sm,
-        "beamspace_ms": {BEAMSPACE_VARIANTS[k]: ms(r.beamspace_ms[k]) for k in range(3)},
+        "beamspace_ms": {BEAMSPACE_VARIANTS[k]: ms(r.beamspace_ms[k]) for k in range(4)},
         "covariance_ms": {COVARIANCE_VARIANTS[k]: ms(r.covariance_ms[k]) for k in range(3)},
         "solve_ms": ms(r.solve_ms), "fused_ms": ms(r.fused_ms),
     }

@@ -260,7 +260,8 @@ bs_status bs_autotune_pass(bs_plan *p, const bs_buffers *b, bs_stream stream, bs
     if (bs_status s = check_device(p)) return s;
     const cudaStream_t st = (cudaStream_t)stream;
     bs_tune_report r;
-    for (int k = 0; k < 3; ++k) r.beamspace_ms[k] = r.covariance_ms[k] = -1.f;
+    for (int k = 0; k < 3; ++k) r.covariance_ms[k] = -1.f;
+    for (int k = 0; k < 4; ++k) r.beamspace_ms[k] = -1.f;
     r.solve_ms = r.fused_ms = -1.f;
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
@@ -286,11 +287,12 @@ bs_status bs_autotune_pass(bs_plan *p, const bs_buffers *b, bs_stream stream, bs
     int best_b = -1;
     float best = 1e30f;
     if (!s && !p->planar) {
-        for (int v = 0; v < 3 && !s; ++v) {
+        for (int v = 0; v < 4 && !s; ++v) {
             const bool applies = (v == 0) ? (p->cfg.M == 1024 || p->cfg.M == 2048 || p->cfg.M == 4096) &&
                                                 p->cfg.N <= 1024 && p->cfg.T <= 256 && !(p->cfg.flags & BS_FLAG_NO_TMA)
                                  : (v == 1) ? p->cfg.M >= 512 && !(p->cfg.N & 1) && !(p->cfg.flags & BS_FLAG_NO_TMA) &&
                                                   (p->Fs % p->vpb) == 0 && (p->B % p->vpb) == 0
+                                 : (v == 3) ? bs::beamspace_tc_applies(p)
                                             : true;
             if (!applies) continue;
             p->tune_beamspace = v;

@@ -197,12 +197,18 @@ bs_status launch_beamspace(const bs_plan *p, const float2 *xc, void *ztr, float2
     if (p->planar) return launch_beamspace2d(p, xc, ga, st);
     bool used = false;
     bs_status s = BS_OK;
-    const int v = p->tune_beamspace;   // -1: the first variant that applies, in this order
-    if (v <= 0) {
+    // -1: the first variant that applies, in the order tensor cores, warp per
+    // transform, bulk-copy-staged, one-shot; 0..3 start the search there
+    const int v = p->tune_beamspace;
+    if (v < 0 || v == 3) {
+        s = launch_beamspace_tc(p, xc, ga, st, &used);
+        if (s || used) return s;
+    }
+    if (v <= 0 || v == 3) {
         s = launch_beamspace_warp(p, xc, ga, st, &used);
         if (s || used) return s;
     }
-    if (v <= 1) {
+    if (v <= 1 || v == 3) {
         s = launch_beamspace_tma(p, xc, ga, st, &used);
         if (s || used) return s;
     }

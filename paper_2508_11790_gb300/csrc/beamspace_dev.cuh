@@ -89,6 +89,11 @@ bs_status launch_beamspace_tma(const bs_plan *p, const float2 *xc, const GatherA
 // BS_FLAG_STAGED_FFT or BS_FLAG_NO_TMA.
 bs_status launch_beamspace_warp(const bs_plan *p, const float2 *xc, const GatherArgs &ga, cudaStream_t st,
                                 bool *used);
+// Tensor-core variant (beamspace_tc.cu) for N = 1024, M = 2048, B even,
+// F (per shard) a multiple of 4 and at most kTabT targets; *used = false
+// otherwise, or with BS_FLAG_SIMT_FFT, BS_FLAG_STAGED_FFT or BS_FLAG_NO_TMA.
+bs_status launch_beamspace_tc(const bs_plan *p, const float2 *xc, const GatherArgs &ga, cudaStream_t st,
+                              bool *used);
 // Planar arrays (beamspace2d.cu): 2-D transform and Wx x Wz window gather.
 bs_status launch_beamspace2d(const bs_plan *p, const float2 *xc, const GatherArgs &ga, cudaStream_t st);
 

@@ -134,6 +134,8 @@ bs_status launch_cov_solve_tables(const void *z, int precision, float store_scal
                                   uint32_t flags, float2 *c, int32_t *info, int *head, int grid,
                                   cudaStream_t st);
 int beamspace_vectors_per_cta(int M);
+// the tensor-core beamspace kernel serves this plan (beamspace_tc.cu)
+bool beamspace_tc_applies(const bs_plan *p);
 bs_status launch_lift(const bs_plan *p, const float2 *c, float2 *c_hat, cudaStream_t st);
 // orthonormal F-point DFT of nvec contiguous rows of F elements (F-point twiddle table)
 bs_status launch_fft_rows(const bs_plan *p, const float2 *y, int64_t nvec, float2 *yb, cudaStream_t st);

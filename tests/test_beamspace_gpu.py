@@ -1,6 +1,7 @@
 """GPU parity of the window beamspace stage (bs_beamspace) for the
-three-pass sizes M = 512 .. 4096: the warp-per-transform kernel (M = 1024,
-2048, 4096 with N <= 1024), the persistent bulk-copy kernel (the other
+three-pass sizes M = 512 .. 4096: the tensor-core kernel (N = 1024,
+M = 2048), the warp-per-transform kernel (M = 1024, 2048, 4096 with
+N <= 1024, and BS_FLAG_SIMT_FFT), the persistent bulk-copy kernel (the other
 sizes, and BS_FLAG_STAGED_FFT) and the one-shot kernel (BS_FLAG_NO_TMA):
 every training and test window against the oracle's zero-padded DFT
 (Eq. VerDFT, Eq. BeamTransform) and window selection (Eq. OverallWindow,
@@ -101,7 +102,8 @@ KERNEL_CASES = CASES[:3] + CASES[-3:]
 
 @pytest.mark.parametrize("case", KERNEL_CASES, ids=[f"N{c[0]}_M{c[1]}" for c in KERNEL_CASES])
 def test_kernels_agree(case):
-    """The default kernel (warp-per-transform where it applies), the
+    """The default kernel (tensor cores or warp-per-transform where they
+    apply), the warp-per-transform kernel (BS_FLAG_SIMT_FFT), the
     bulk-copy-staged kernel (BS_FLAG_STAGED_FFT) and the one-shot kernel
     (BS_FLAG_NO_TMA) factor the transform differently and read their
     twiddles differently (table values, products of table values, folded
@@ -113,7 +115,7 @@ def test_kernels_agree(case):
     xc = (rng.standard_normal((Pn, F, N)) + 1j * rng.standard_normal((Pn, F, N))).astype(np.complex64)
     u = list(rng.uniform(-0.9, 0.9, size=len(W)))
     outs = []
-    for flags in (0, P.BS_FLAG_STAGED_FFT, P.BS_FLAG_NO_TMA):
+    for flags in (0, P.BS_FLAG_SIMT_FFT, P.BS_FLAG_STAGED_FFT, P.BS_FLAG_NO_TMA):
         plan, off, ztr, zte = _run_beamspace(N, M, F, L, Ptr, Pte, W, K, u, P.BS_PREC_FP32, flags, xc)
         _check_windows(plan, off, ztr, zte, xc, M, L, Ptr, Pte, P.BS_PREC_FP32)
         outs.append((ztr, zte))
@@ -157,3 +159,25 @@ def test_many_targets_gather_paths():
         ss = 2.0 if precision != P.BS_PREC_FP32 else 0.0
         plan, off, ztr, zte = _run_beamspace(N, M, F, L, Ptr, Pte, W, K, u, precision, 0, xc, ss)
         _check_windows(plan, off, ztr, zte, xc, M, L, Ptr, Pte, precision)
+
+
+def test_tensor_core_input_scale():
+    """The tensor-core kernel scales every vector by a power of two before
+    splitting it into FP16 parts, so inputs scaled by 2^-40 or 2^40 (far
+    outside FP16's range) give windows scaled by exactly that power of two,
+    and any other scale factor stays within the FFT bound of the oracle."""
+    N, M, F, L, Ptr, Pte, W, K = 1024, 2048, 256, 16, 2, 1, [9, 32, 1], [32, 17, 5]
+    rng = np.random.default_rng(2048)
+    Pn = Ptr + Pte
+    xc = (rng.standard_normal((Pn, F, N)) + 1j * rng.standard_normal((Pn, F, N))).astype(np.complex64)
+    xc[:, :, :7] *= 3e3   # a strong component on a few elements
+    u = [0.0, 0.37, -0.8]
+    _, _, ztr0, zte0 = _run_beamspace(N, M, F, L, Ptr, Pte, W, K, u, P.BS_PREC_FP32, 0, xc)
+    for e in (-40, 40):
+        _, _, ztr, zte = _run_beamspace(N, M, F, L, Ptr, Pte, W, K, u, P.BS_PREC_FP32, 0,
+                                        (xc * np.float32(2.0 ** e)).astype(np.complex64))
+        assert np.array_equal(ztr, ztr0 * 2.0 ** e) and np.array_equal(zte, zte0 * 2.0 ** e)
+    for f in (1e-30, 7.3e25):
+        xs = (xc * np.float32(f)).astype(np.complex64)
+        plan, off, ztr, zte = _run_beamspace(N, M, F, L, Ptr, Pte, W, K, u, P.BS_PREC_FP32, 0, xs)
+        _check_windows(plan, off, ztr, zte, xs, M, L, Ptr, Pte, P.BS_PREC_FP32)
