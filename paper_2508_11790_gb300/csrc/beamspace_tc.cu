@@ -29,14 +29,16 @@
 // instruction for both vectors.  The beams go to shared memory, and all
 // threads then store the windows.
 //
-// One CTA per SM, 13 warps: warps 0-7 read the accumulators (warp w reads
-// tensor-memory lanes 32 (w mod 4) .. + 31 of vector pair w / 4), warps 8-11
-// scale and split one vector each of the tile after next (each vector
-// arrives by one bulk copy, issued a tile ahead) and build the per-target
-// gather entries, and warp 12 issues the products.  The
-// first twelve share the window stores and meet at a named barrier twice
-// per tile; the MMA warp follows mbarriers only (stage written, accumulator
-// read, products done), so its waits on the tensor pipe stall nobody else.
+// One CTA per SM, 13 warps: warps 0-7 are two epilogue groups (warp w reads
+// tensor-memory lanes 32 (w mod 4) .. + 31 for vector pair w / 4 and then
+// stores that pair's windows), warps 8-11 scale and split one vector each
+// of the tile after next (each vector arrives by one bulk copy, issued a
+// tile ahead) and write the per-target gather entries of the current tile,
+// and warp 12 issues the products.  The roles hand work over through
+// mbarriers only (stage written, accumulator read, products done, entries
+// written, windows stored), and an epilogue group meets only itself at a
+// named barrier, so one group's stores overlap the other's arithmetic and
+// the MMA warp's waits on the tensor pipe stall nobody else.
 // Two accumulators and two B stages let the tensor cores work on tiles
 // i + 1 and i + 2 while the CUDA cores finish tile i.  Every wait on an
 // mbarrier is bounded; a wait that gives up sets bit 0 of the plan's error
@@ -52,7 +54,6 @@ namespace bs {
 namespace {
 
 constexpr int kTcThreads = 416;   // 8 epilogue warps, 4 producer warps, 1 MMA warp
-constexpr int kTcWork = 384;      // threads of the epilogue and producer warps (they share the gather)
 constexpr int kTcVec = 4;     // vectors per tile
 constexpr int kTcN = 64;      // MMA N: 4 vectors x 16 columns n2
 // shared memory (bytes)
@@ -61,12 +62,13 @@ constexpr int kSmBStage = 32768;
 constexpr int kSmBMat = 8192;
 constexpr int kSmBeam = 2 * kSmBStage;           // 2 vector pairs x {re, im} x 2048 beams x float2
 constexpr int kSmBeamPair = 2 * 2048 * 8;
-constexpr int kSmTab = kSmBeam + 2 * kSmBeamPair;  // [2 pairs][kTabT] TabEnt
-constexpr int kSmTw = kSmTab + 2 * kTabT * 8;     // [16 n2][128 k] W_M^(n2 k) (row 0 unused)
+constexpr int kSmTab = kSmBeam + 2 * kSmBeamPair;  // [2 tiles][2 pairs][kTabT] TabEnt
+constexpr int kSmTw = kSmTab + 4 * kTabT * 8;     // [16 n2][128 k] W_M^(n2 k) (row 0 unused)
 constexpr int kSmRaw = kSmTw + 16 * 128 * 8;     // [4 vectors][1024] float2: the producers' bulk-copied inputs
 constexpr int kSmMisc = kSmRaw + 4 * 8192;
 constexpr int kSmGlist = kSmMisc + 256;             // [sumW] gather entry list (dynamic size)
 constexpr int kSmTotalMax = kSmGlist + 4 * kTabT * 32;
+static_assert(kSmTotalMax <= 227 * 1024, "shared memory");
 // tensor memory columns: accumulators 2 x {Re Y [64], Im Y [64]}, then the
 // A operand: ReD hi, ReD lo, ImD hi, ImD lo, -ImD hi, -ImD lo (32 columns
 // of two FP16 values each per row)
@@ -166,8 +168,13 @@ __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t
                  : "memory");
 }
 
-// Barrier of the epilogue and producer warps, reached from their two loops.
-__device__ __forceinline__ void cta_bar() { asm volatile("bar.sync 2, 384;" ::: "memory"); }
+// Barrier of the four epilogue warps of vector pair g (named barriers 3, 4).
+__device__ __forceinline__ void group_bar(int g) {
+    if (g == 0)
+        asm volatile("bar.sync 3, 128;" ::: "memory");
+    else
+        asm volatile("bar.sync 4, 128;" ::: "memory");
+}
 
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
@@ -318,13 +325,15 @@ __device__ __forceinline__ void prep_store(const PrepRegs &r, uint32_t stage, fl
 }
 
 // Gather entries of the tile's two vector pairs (both vectors of a pair are
-// neighbouring bins of one subband and one record): the per-pair fields of
-// the tile's subband are fetched one tile ahead (their loads then overlap
-// the window stores of the current tile) and written out when the tile
-// comes up.  Producer thread tp handles entries tp + 128 j (T <= 256).
+// neighbouring bins of one subband and one record), written by the producer
+// warps: the per-pair fields of the tile's subband are fetched one tile
+// ahead (the loads overlap the producer's other work) and written out when
+// the tile comes up.  Producer thread tp handles entries tp + 128 j
+// (T <= 256).
+constexpr int kTabPerThread = 2 * kTabT / 128;
 struct TabFetch {
-    long long off[4];   // ztr_off or zte_off of the pair (whichever the tile's record uses)
-    int sw[4], K[4];    // start | (W << 16), training vectors
+    long long off[kTabPerThread];   // ztr_off or zte_off of the pair (whichever the tile's record uses)
+    int sw[kTabPerThread], K[kTabPerThread];   // start | (W << 16), training vectors
 };
 
 __device__ __forceinline__ void tile_subband(const GatherArgs &ga, int64_t vec0, int p, int &sb, bool &train,
@@ -340,7 +349,7 @@ __device__ __forceinline__ void tile_subband(const GatherArgs &ga, int64_t vec0,
 
 __device__ __forceinline__ void tab_fetch(const GatherArgs &ga, int64_t vec0, TabFetch &f, int tp) {
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < kTabPerThread; ++j) {
         const int idx = tp + 128 * j;
         if (idx < 2 * ga.T) {
             const int p = idx >= ga.T ? 1 : 0;
@@ -359,7 +368,7 @@ __device__ __forceinline__ void tab_fetch(const GatherArgs &ga, int64_t vec0, Ta
 __device__ __forceinline__ void tab_write(const GatherArgs &ga, int64_t vec0, const TabFetch &f, TabEnt *tab,
                                           int tp) {
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < kTabPerThread; ++j) {
         const int idx = tp + 128 * j;
         if (idx < 2 * ga.T) {
             const int p = idx >= ga.T ? 1 : 0;
@@ -481,18 +490,18 @@ __device__ __forceinline__ void gather_entry(const GatherArgs &ga, bool train, f
     }
 }
 
+// The window stores of vector pair p by its epilogue group (thread gt of
+// 128), two entries per iteration.
 template <int PREC>
-__device__ __forceinline__ void gather_tile(const TcArgs &a, const GatherArgs &ga, bool train, const int *glist,
-                                            const TabEnt *tab, const float2 *beams, const float *vsc, int tid) {
+__device__ __forceinline__ void gather_pair(const TcArgs &a, const GatherArgs &ga, bool train, const int *glist,
+                                            const TabEnt *tab, const float2 *beams, const float *vsc, int p, int gt) {
     const float ss = (train && PREC != BS_PREC_FP32) ? a.store_scale : 1.f;
-    const int total = 2 * a.sumW;
-    for (int e = tid; e < total; e += 2 * kTcWork) {
-        const int e1 = e + kTcWork;
-        const int p0 = e >= a.sumW ? 1 : 0, p1 = e1 >= a.sumW ? 1 : 0;
-        const int pk0 = glist[e - p0 * a.sumW];
-        const int pk1 = e1 < total ? glist[e1 - p1 * a.sumW] : -1;
-        gather_entry<PREC>(ga, train, ss, tab, beams, vsc, p0, pk0);
-        if (pk1 >= 0) gather_entry<PREC>(ga, train, ss, tab, beams, vsc, p1, pk1);
+    for (int e = gt; e < a.sumW; e += 256) {
+        const int e1 = e + 128;
+        const int pk0 = glist[e];
+        const int pk1 = e1 < a.sumW ? glist[e1] : -1;
+        gather_entry<PREC>(ga, train, ss, tab, beams, vsc, p, pk0);
+        if (pk1 >= 0) gather_entry<PREC>(ga, train, ss, tab, beams, vsc, p, pk1);
     }
 }
 
@@ -502,17 +511,21 @@ template <int PREC>
 __global__ void __launch_bounds__(kTcThreads, 1) beamspace_tc_kernel(TcArgs a, GatherArgs ga) {
     extern __shared__ __align__(1024) unsigned char smtc[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    // mbarriers: done[b] (the products into accumulator b are complete; one
-    // commit), full[b] (stage b written: 128 producer threads), freed[b]
-    // (accumulator b read: 256 epilogue threads)
+    // mbarriers: done[b] (products into accumulator b complete; one commit),
+    // full[b] (stage b written; 128 producer threads), freed[b] (accumulator
+    // b read; 256 epilogue threads), tabfull[b] (gather entries of the tile
+    // written; 128 producers), tabfree[b] (that tile's windows stored; 256
+    // epilogue threads), rawbar[v] (producer v's input copy landed)
     uint64_t *done = reinterpret_cast<uint64_t *>(smtc + kSmMisc);
     uint64_t *full = done + 2;
     uint64_t *freed = done + 4;
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(smtc + kSmMisc + 48);
-    int *abort_flag = reinterpret_cast<int *>(smtc + kSmMisc + 52);
-    float *vsc = reinterpret_cast<float *>(smtc + kSmMisc + 64);        // [4 tiles][4 vectors]
-    uint64_t *rawbar = reinterpret_cast<uint64_t *>(smtc + kSmMisc + 128);   // [4]: producer input copies
-    TabEnt *tab = reinterpret_cast<TabEnt *>(smtc + kSmTab);            // [2 pairs][kTabT]
+    uint64_t *tabfull = done + 6;
+    uint64_t *tabfree = done + 8;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(smtc + kSmMisc + 80);
+    int *gflag = reinterpret_cast<int *>(smtc + kSmMisc + 84);           // [2]: a group's wait gave up
+    float *vsc = reinterpret_cast<float *>(smtc + kSmMisc + 96);        // [4 tiles][4 vectors]
+    uint64_t *rawbar = reinterpret_cast<uint64_t *>(smtc + kSmMisc + 160);   // [4]
+    TabEnt *tabs = reinterpret_cast<TabEnt *>(smtc + kSmTab);           // [2 tiles][2 pairs][kTabT]
     float2 *beams = reinterpret_cast<float2 *>(smtc + kSmBeam);         // [2 pairs][re, im][2048]
     auto train_of = [&](int64_t vec0) { return (int)((ga.vbase + vec0) >> ga.log2F) < ga.P_train; };
     const uint32_t sbase = smem_u32(smtc);
@@ -526,9 +539,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) beamspace_tc_kernel(TcArgs a, G
             mbar_init(&done[j], 1);
             mbar_init(&full[j], 128);
             mbar_init(&freed[j], 256);
+            mbar_init(&tabfull[j], 128);
+            mbar_init(&tabfree[j], 256);
+            gflag[j] = 0;
         }
         for (int j = 0; j < 4; ++j) mbar_init(&rawbar[j], 1);
-        *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) tmem_alloc(tslot, kTmCols);
@@ -536,36 +551,45 @@ __global__ void __launch_bounds__(kTcThreads, 1) beamspace_tc_kernel(TcArgs a, G
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tslot;
-
     int *glist = reinterpret_cast<int *>(smtc + kSmGlist);
     for (int e = tid; e < a.sumW; e += kTcThreads) glist[e] = __ldg(&a.glist[e]);
+
     if (warp < 8) {
-        // ---- epilogue warps: accumulator rows k of vector pair warp / 4
-        const int q = warp & 3, k = 32 * q + lane, p = warp >> 2;
+        // ---- epilogue group g = warp / 4: accumulator rows k of vector pair
+        // g, then that pair's window stores; the two groups run independently
+        const int q = warp & 3, k = 32 * q + lane, g = warp >> 2, gt = tid & 127;
         float2 *tws = reinterpret_cast<float2 *>(smtc + kSmTw);
         if (warp < 4) {
             write_dft_rows(tmem, a.tw, q, k);
             for (int n2 = 1; n2 < 16; ++n2) tws[n2 * 128 + k] = __ldg(&a.tw[(n2 * k) & 2047]);
         }
         tc_fence_before();
-        __syncthreads();   // A rows in tensor memory
+        __syncthreads();   // A rows in tensor memory, twiddles and entry list in shared memory
+        float2 *pb = beams + g * (kSmBeamPair / 8);
         for (int i = 0; i < nt; ++i) {
             const int b = i & 1;
-            if (mbar_wait_bounded(&done[b], (unsigned)(i >> 1) & 1u)) {
+            const unsigned ph = (unsigned)(i >> 1) & 1u;
+            if (mbar_wait_bounded(&done[b], ph)) {
                 tc_fence_after();
-                epilogue(tmem + ((uint32_t)(32 * q) << 16) + 128 * b + 32 * p, tws,
-                         beams + p * (kSmBeamPair / 8), k, &freed[b]);
+                epilogue(tmem + ((uint32_t)(32 * q) << 16) + 128 * b + 32 * g, tws, pb, k, &freed[b]);
             } else {
-                atomicOr(a.err, 1);
-                *abort_flag = 1;
+                gflag[g] = 1;
             }
-            cta_bar();   // beams, gather entries and scales of tile i ready
-            if (*abort_flag) break;
-            gather_tile<PREC>(a, ga, train_of(vec0_of(i)), glist, tab, beams, vsc + 4 * (i & 3), tid);
-            cta_bar();   // beams and entries free
+            group_bar(g);   // beams of the pair ready
+            if (gflag[g]) break;
+            if (mbar_wait_bounded(&tabfull[b], ph))
+                gather_pair<PREC>(a, ga, train_of(vec0_of(i)), glist, tabs + b * 2 * kTabT, beams, vsc + 4 * (i & 3),
+                                  g, gt);
+            else
+                gflag[g] = 1;
+            mbar_arrive(&tabfree[b]);
+            group_bar(g);   // beams free
+            if (gflag[g]) break;
         }
+        if (gflag[g] && gt == 0) atomicOr(a.err, 1);
     } else if (warp < 12) {
-        // ---- producer warps: vector v = warp - 8 of the tile after next
+        // ---- producer warps: vector v = warp - 8 of the tile after next, and
+        // the gather entries of the current tile
         const int v = warp - 8, tp = tid - 256;
         float2 *raw = reinterpret_cast<float2 *>(smtc + kSmRaw) + v * 1024;
         uint64_t *rbar = rawbar + v;
@@ -583,35 +607,29 @@ __global__ void __launch_bounds__(kTcThreads, 1) beamspace_tc_kernel(TcArgs a, G
             mbar_arrive(&full[i]);
             __syncwarp();   // every lane has read the slot before it is refilled
         }
-        if (!ok) {
-            atomicOr(a.err, 1);
-            *abort_flag = 1;
-        } else if (nt > 2) {
-            prep_fetch(raw, rbar, a.y, vec0_of(2) + v, lane);
-        }
-        for (int i = 0; i < nt; ++i) {
+        if (ok && nt > 2) prep_fetch(raw, rbar, a.y, vec0_of(2) + v, lane);
+        for (int i = 0; i < nt && ok; ++i) {
             const int b = i & 1;
-            tab_write(ga, vec0_of(i), tf, tab, tp);
-            if (i + 2 < nt && ok) {   // stage b is free once the products of tile i are done
-                ok = mbar_wait_bounded(&done[b], (unsigned)(i >> 1) & 1u) &&
-                     mbar_wait_bounded(rbar, (unsigned)(i + 2) & 1u);
-                if (ok) {
-                    prep_read(pr, raw, lane);
-                    prep_store(pr, sbase + kSmB + b * kSmBStage, vsc + 4 * ((i + 2) & 3), v, lane, post);
-                    mbar_arrive(&full[b]);
-                    __syncwarp();
-                    if (i + 3 < nt) prep_fetch(raw, rbar, a.y, vec0_of(i + 3) + v, lane);
-                } else {
-                    atomicOr(a.err, 1);
-                    *abort_flag = 1;
-                }
-            }
-            cta_bar();
-            if (*abort_flag) break;
+            // entries of tile i into buffer b once tile i - 2's windows are stored
+            if (i >= 2) ok = mbar_wait_bounded(&tabfree[b], (unsigned)((i >> 1) - 1) & 1u);
+            if (!ok) break;
+            tab_write(ga, vec0_of(i), tf, tabs + b * 2 * kTabT, tp);
+            mbar_arrive(&tabfull[b]);
             if (i + 1 < nt) tab_fetch(ga, vec0_of(i + 1), tf, tp);
-            gather_tile<PREC>(a, ga, train_of(vec0_of(i)), glist, tab, beams, vsc + 4 * (i & 3), tid);
-            cta_bar();
+            if (i + 2 < nt) {   // tile i + 2 into stage b once the products of tile i are done
+                ok = mbar_wait_bounded(rbar, (unsigned)i & 1u);
+                if (!ok) break;
+                prep_read(pr, raw, lane);
+                fence_proxy_async();   // the reads complete before the slot is refilled by the async proxy
+                __syncwarp();
+                if (i + 3 < nt) prep_fetch(raw, rbar, a.y, vec0_of(i + 3) + v, lane);
+                ok = mbar_wait_bounded(&done[b], (unsigned)(i >> 1) & 1u);
+                if (!ok) break;
+                prep_store(pr, sbase + kSmB + b * kSmBStage, vsc + 4 * ((i + 2) & 3), v, lane, post);
+                mbar_arrive(&full[b]);
+            }
         }
+        if (!ok && lane == 0) atomicOr(a.err, 1);
     } else {
         // ---- MMA warp: products of tile i into accumulator i mod 2 once stage
         // i mod 2 is written and (from tile 2 on) the accumulator has been read
@@ -621,7 +639,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) beamspace_tc_kernel(TcArgs a, G
             const unsigned u = (unsigned)(i >> 1);
             bool ok = mbar_wait_bounded(&full[b], u & 1u);
             if (ok && i >= 2) ok = mbar_wait_bounded(&freed[b], (u - 1) & 1u);
-            if (!ok) {   // the other warps then give up on done[] and stop together
+            if (!ok) {   // the other warps then give up on their waits
                 if (lane == 0) atomicOr(a.err, 1);
                 break;
             }
