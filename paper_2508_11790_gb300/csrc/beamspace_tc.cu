@@ -30,8 +30,8 @@
 // threads then store the windows.
 //
 // One CTA per SM, 13 warps: warps 0-7 are two epilogue groups (warp w reads
-// tensor-memory lanes 32 (w mod 4) .. + 31 for vector pair w / 4 and then
-// stores that pair's windows), warps 8-11 scale and split one vector each
+// tensor-memory lanes 32 (w mod 4) .. + 31 of the tiles of parity w / 4,
+// one vector pair at a time, and stores the pair's windows), warps 8-11 scale and split one vector each
 // of the tile after next (each vector arrives by one bulk copy, issued a
 // tile ahead) and write the per-target gather entries of the current tile,
 // and warp 12 issues the products.  The roles hand work over through
@@ -417,8 +417,10 @@ __device__ __noinline__ void write_dft_rows(uint32_t tmem, const float2 *__restr
 __device__ __forceinline__ void epilogue(uint32_t tacc, const float2 *tw, float2 *beam, int k, uint64_t *freed) {
     float re[32], im[32];
     tmem_ld2x32(tacc, tacc + 64, re, im);
-    tc_fence_before();
-    mbar_arrive(freed);   // the accumulator may be overwritten
+    if (freed) {
+        tc_fence_before();
+        mbar_arrive(freed);   // the accumulator may be overwritten
+    }
     float2 R[16], I[16];
 #pragma unroll
     for (int n2 = 0; n2 < 16; ++n2) {
@@ -476,7 +478,7 @@ __device__ __forceinline__ void gather_entry(const GatherArgs &ga, bool train, f
     if (n == 0) return;
     const int w = pk & 255;
     const int m = ((te.swn & 2047) + w) & 2047;
-    const float2 *bp = beams + p * (kSmBeamPair / 8) + m;
+    const float2 *bp = beams + m;
     const float2 sc = make_float2(vsc[2 * p] * ss, vsc[2 * p + 1] * ss);
     const float2 re = __fmul2_rn(bp[0], sc), im = __fmul2_rn(bp[2048], sc);
     const int i0 = te.base + w;
@@ -538,9 +540,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) beamspace_tc_kernel(TcArgs a, G
         for (int j = 0; j < 2; ++j) {
             mbar_init(&done[j], 1);
             mbar_init(&full[j], 128);
-            mbar_init(&freed[j], 256);
+            mbar_init(&freed[j], 128);
             mbar_init(&tabfull[j], 128);
-            mbar_init(&tabfree[j], 256);
+            mbar_init(&tabfree[j], 128);
             gflag[j] = 0;
         }
         for (int j = 0; j < 4; ++j) mbar_init(&rawbar[j], 1);
@@ -555,8 +557,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) beamspace_tc_kernel(TcArgs a, G
     for (int e = tid; e < a.sumW; e += kTcThreads) glist[e] = __ldg(&a.glist[e]);
 
     if (warp < 8) {
-        // ---- epilogue group g = warp / 4: accumulator rows k of vector pair
-        // g, then that pair's window stores; the two groups run independently
+        // ---- epilogue group g = warp / 4 takes the tiles i = g mod 2 (their
+        // accumulator is g): for vector pair 0, then pair 1, accumulator rows
+        // k into the group's beam buffer and then that pair's window stores.
+        // The two groups work on different tiles, so one group's stores
+        // overlap the other's arithmetic.
         const int q = warp & 3, k = 32 * q + lane, g = warp >> 2, gt = tid & 127;
         float2 *tws = reinterpret_cast<float2 *>(smtc + kSmTw);
         if (warp < 4) {
@@ -566,25 +571,28 @@ __global__ void __launch_bounds__(kTcThreads, 1) beamspace_tc_kernel(TcArgs a, G
         tc_fence_before();
         __syncthreads();   // A rows in tensor memory, twiddles and entry list in shared memory
         float2 *pb = beams + g * (kSmBeamPair / 8);
-        for (int i = 0; i < nt; ++i) {
-            const int b = i & 1;
+        for (int i = g; i < nt; i += 2) {
             const unsigned ph = (unsigned)(i >> 1) & 1u;
-            if (mbar_wait_bounded(&done[b], ph)) {
-                tc_fence_after();
-                epilogue(tmem + ((uint32_t)(32 * q) << 16) + 128 * b + 32 * g, tws, pb, k, &freed[b]);
-            } else {
-                gflag[g] = 1;
+            bool ok = mbar_wait_bounded(&done[g], ph);
+            for (int p = 0; p < 2; ++p) {
+                if (ok) {
+                    tc_fence_after();
+                    epilogue(tmem + ((uint32_t)(32 * q) << 16) + 128 * g + 32 * p, tws, pb, k,
+                             p == 1 ? &freed[g] : nullptr);
+                } else {
+                    gflag[g] = 1;
+                }
+                group_bar(g);   // beams of pair p ready
+                if (gflag[g]) break;
+                if (p == 0 && !mbar_wait_bounded(&tabfull[g], ph)) gflag[g] = 1;
+                else
+                    gather_pair<PREC>(a, ga, train_of(vec0_of(i)), glist, tabs + g * 2 * kTabT, pb,
+                                      vsc + 4 * (i & 3), p, gt);
+                group_bar(g);   // beams free
+                if (gflag[g]) break;
             }
-            group_bar(g);   // beams of the pair ready
             if (gflag[g]) break;
-            if (mbar_wait_bounded(&tabfull[b], ph))
-                gather_pair<PREC>(a, ga, train_of(vec0_of(i)), glist, tabs + b * 2 * kTabT, beams, vsc + 4 * (i & 3),
-                                  g, gt);
-            else
-                gflag[g] = 1;
-            mbar_arrive(&tabfree[b]);
-            group_bar(g);   // beams free
-            if (gflag[g]) break;
+            mbar_arrive(&tabfree[g]);
         }
         if (gflag[g] && gt == 0) atomicOr(a.err, 1);
     } else if (warp < 12) {
