@@ -466,24 +466,24 @@ __device__ __forceinline__ void issue_tile(uint32_t tmem, int buf, uint32_t stag
     mma_commit(bar);
 }
 
-// Window stores of one tile: every (pair, target, w) entry reads beam
-// start + w of both vectors of the pair and stores the rows that exist.
-// The entry list (t << 8) | w sits in shared memory; two entries per
-// iteration keep two load chains in flight.
-template <int PREC>
-__device__ __forceinline__ void gather_entry(const GatherArgs &ga, bool train, float ss, const TabEnt *tab,
-                                             const float2 *beams, const float *vsc, int p, int pk) {
-    const TabEnt te = tab[p * kTabT + (pk >> 8)];
+// Window stores of vector pair p of a tile by its epilogue group (thread
+// gt of 128): every (target, w) entry of the list (t << 8) | w reads beam
+// start + w of both vectors of the pair from the group's beam buffer and
+// stores the rows that exist.  Two entries per iteration keep two load
+// chains in flight; TRAIN selects the window array (training rows in the
+// plan precision, test rows in FP32).
+template <int PREC, bool TRAIN>
+__device__ __forceinline__ void gather_entry(const GatherArgs &ga, float2 sc, const TabEnt *tab, const float2 *beams,
+                                             int pk) {
+    const TabEnt te = tab[pk >> 8];
     const int n = te.swn >> 17;
     if (n == 0) return;
     const int w = pk & 255;
-    const int m = ((te.swn & 2047) + w) & 2047;
-    const float2 *bp = beams + m;
-    const float2 sc = make_float2(vsc[2 * p] * ss, vsc[2 * p + 1] * ss);
+    const float2 *bp = beams + (((te.swn & 2047) + w) & 2047);
     const float2 re = __fmul2_rn(bp[0], sc), im = __fmul2_rn(bp[2048], sc);
     const int i0 = te.base + w;
     const int W = (te.swn >> 11) & 63;
-    if (train) {
+    if (TRAIN) {
         store_train<PREC>(ga.ztr, i0, make_float2(re.x, im.x), 1.f);
         if (n > 1) store_train<PREC>(ga.ztr, i0 + W, make_float2(re.y, im.y), 1.f);
     } else {
@@ -492,19 +492,27 @@ __device__ __forceinline__ void gather_entry(const GatherArgs &ga, bool train, f
     }
 }
 
-// The window stores of vector pair p by its epilogue group (thread gt of
-// 128), two entries per iteration.
+template <int PREC, bool TRAIN>
+__device__ __forceinline__ void gather_loop(const GatherArgs &ga, int sumW, const int *glist, float2 sc,
+                                            const TabEnt *tab, const float2 *beams, int gt) {
+    for (int e = gt; e < sumW; e += 256) {
+        const int e1 = e + 128;
+        const int pk0 = glist[e];
+        const int pk1 = e1 < sumW ? glist[e1] : -1;
+        gather_entry<PREC, TRAIN>(ga, sc, tab, beams, pk0);
+        if (pk1 >= 0) gather_entry<PREC, TRAIN>(ga, sc, tab, beams, pk1);
+    }
+}
+
 template <int PREC>
 __device__ __forceinline__ void gather_pair(const TcArgs &a, const GatherArgs &ga, bool train, const int *glist,
                                             const TabEnt *tab, const float2 *beams, const float *vsc, int p, int gt) {
     const float ss = (train && PREC != BS_PREC_FP32) ? a.store_scale : 1.f;
-    for (int e = gt; e < a.sumW; e += 256) {
-        const int e1 = e + 128;
-        const int pk0 = glist[e];
-        const int pk1 = e1 < a.sumW ? glist[e1] : -1;
-        gather_entry<PREC>(ga, train, ss, tab, beams, vsc, p, pk0);
-        if (pk1 >= 0) gather_entry<PREC>(ga, train, ss, tab, beams, vsc, p, pk1);
-    }
+    const float2 sc = make_float2(vsc[2 * p] * ss, vsc[2 * p + 1] * ss);
+    if (train)
+        gather_loop<PREC, true>(ga, a.sumW, glist, sc, tab + p * kTabT, beams, gt);
+    else
+        gather_loop<PREC, false>(ga, a.sumW, glist, sc, tab + p * kTabT, beams, gt);
 }
 
 // --------------------------------------------------------------------- kernel
