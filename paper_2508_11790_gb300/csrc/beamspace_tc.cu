@@ -18,7 +18,7 @@
 // product); every vector is scaled by the power of two that brings its
 // largest component into [2^13, 2^14), so both parts of the data stay in
 // FP16's normal range whatever the input scale.  The DFT matrix (its real
-// part, imaginary part and negated imaginary part, high and low) is the A
+// and imaginary parts, high and low) is the A
 // operand and lives in tensor memory for the whole kernel; the vectors are
 // the B operand, staged in shared memory in the canonical K-major layout.
 //
@@ -39,8 +39,8 @@
 // written, windows stored), and an epilogue group meets only itself at a
 // named barrier, so one group's stores overlap the other's arithmetic and
 // the MMA warp's waits on the tensor pipe stall nobody else.
-// Two accumulators and two B stages let the tensor cores work on tiles
-// i + 1 and i + 2 while the CUDA cores finish tile i.  Every wait on an
+// Three accumulators and two B stages let the tensor cores work on the
+// next tiles while the CUDA cores finish the current ones.  Every wait on an
 // mbarrier is bounded; a wait that gives up sets bit 0 of the plan's error
 // word and the CTA stops after freeing its tensor memory.
 #include "beamspace_dev.cuh"
@@ -69,11 +69,12 @@ constexpr int kSmMisc = kSmRaw + 4 * 8192;
 constexpr int kSmGlist = kSmMisc + 256;             // [sumW] gather entry list (dynamic size)
 constexpr int kSmTotalMax = kSmGlist + 4 * kTabT * 32;
 static_assert(kSmTotalMax <= 227 * 1024, "shared memory");
-// tensor memory columns: accumulators 2 x {Re Y [64], Im Y [64]}, then the
-// A operand: ReD hi, ReD lo, ImD hi, ImD lo, -ImD hi, -ImD lo (32 columns
-// of two FP16 values each per row)
+// tensor memory columns: three accumulators {Re Y [64], Im Y [64]}, then
+// the A operand: ReD hi, ReD lo, ImD hi, ImD lo (32 columns of two FP16
+// values each per row)
 constexpr uint32_t kTmCols = 512;
-constexpr uint32_t kTmA = 256;
+constexpr int kTcAcc = 3;
+constexpr uint32_t kTmA = 128 * kTcAcc;
 
 // Gather entry of a target for one vector pair: window-array offset of the
 // pair's even vector, and start | (W << 11) | (stores << 17), where stores
@@ -388,12 +389,12 @@ __device__ __forceinline__ void tab_write(const GatherArgs &ga, int64_t vec0, co
 // ------------------------------------------------------------ epilogue side
 
 // Row k of the DFT matrix D[k][n1] = W_128^(n1 k) into tensor memory (this
-// warp's lanes): ReD, ImD, -ImD, each as FP16 high and low parts, two n1 per
+// warp's lanes): ReD and ImD, each as FP16 high and low parts, two n1 per
 // 32-bit column.
 __device__ __noinline__ void write_dft_rows(uint32_t tmem, const float2 *__restrict__ tw, int q, int k) {
     const uint32_t lanebits = (uint32_t)(32 * q) << 16;
 #pragma unroll 1
-    for (int mat = 0; mat < 6; ++mat) {
+    for (int mat = 0; mat < 4; ++mat) {
         uint32_t w[32];
 #pragma unroll
         for (int cc = 0; cc < 32; ++cc) {
@@ -401,7 +402,7 @@ __device__ __noinline__ void write_dft_rows(uint32_t tmem, const float2 *__restr
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
                 const float2 d = __ldg(&tw[16 * ((k * (2 * cc + u)) & 127)]);
-                const float val = (mat < 2) ? d.x : (mat < 4 ? d.y : -d.y);
+                const float val = (mat < 2) ? d.x : d.y;
                 const float hi = __half2float(__float2half_rn(val));
                 v[u] = (mat & 1) ? val - hi : hi;
             }
@@ -444,24 +445,27 @@ __device__ __forceinline__ void epilogue(uint32_t tacc, const float2 *tw, float2
 }
 
 // The 48 products of one tile (N = 64 columns, K = 64 in four slices of 16):
-//   Re Y = ReD Xre + (-ImD) Xim,  Im Y = ImD Xre + ReD Xim,
-// each as hi*hi + hi*lo + lo*hi; then one commit to `bar`.
-__device__ __forceinline__ void issue_tile(uint32_t tmem, int buf, uint32_t stage, uint64_t *bar) {
+//   Re Y = ReD Xre - ImD Xim,  Im Y = ImD Xre + ReD Xim,
+// each as hi*hi + hi*lo + lo*hi (the minus through the instruction's
+// negate-A bit); then one commit to `bar`.
+__device__ __forceinline__ void issue_tile(uint32_t tmem, int acc, uint32_t stage, uint64_t *bar) {
     constexpr uint32_t idesc = (1u << 4)                                  // D: FP32
                                | ((uint32_t)(kTcN >> 3) << 17)            // N
                                | ((uint32_t)(128 >> 4) << 24);            // M; A, B: FP16, K-major
-    // A: 0 ReD hi, 1 ReD lo, 2 ImD hi, 3 ImD lo, 4 -ImD hi, 5 -ImD lo; B: 0 Xre hi, 1 Xre lo, 2 Xim hi, 3 Xim lo
-    constexpr int kA[2][6] = {{0, 0, 1, 4, 4, 5}, {2, 2, 3, 0, 0, 1}};
+    constexpr uint32_t kNegA = 1u << 13;
+    // A: 0 ReD hi, 1 ReD lo, 2 ImD hi, 3 ImD lo; B: 0 Xre hi, 1 Xre lo, 2 Xim hi, 3 Xim lo
+    constexpr int kA[2][6] = {{0, 0, 1, 2, 2, 3}, {2, 2, 3, 0, 0, 1}};
     constexpr int kB[2][6] = {{0, 1, 0, 2, 3, 2}, {0, 1, 0, 2, 3, 2}};
 #pragma unroll
     for (int part = 0; part < 2; ++part) {
-        const uint32_t d = tmem + 128 * buf + 64 * part;
+        const uint32_t d = tmem + 128 * acc + 64 * part;
 #pragma unroll
         for (int t = 0; t < 6; ++t)
 #pragma unroll
             for (int j = 0; j < 4; ++j)
                 mma_ts(d, tmem + kTmA + 32 * kA[part][t] + 8 * j,
-                       smem_desc(stage + kSmBMat * kB[part][t] + 256 * j), idesc, t | j);
+                       smem_desc(stage + kSmBMat * kB[part][t] + 256 * j),
+                       (part == 0 && t >= 3) ? (idesc | kNegA) : idesc, t | j);
     }
     mma_commit(bar);
 }
@@ -521,20 +525,22 @@ template <int PREC>
 __global__ void __launch_bounds__(kTcThreads, 1) beamspace_tc_kernel(TcArgs a, GatherArgs ga) {
     extern __shared__ __align__(1024) unsigned char smtc[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    // mbarriers: done[b] (products into accumulator b complete; one commit),
-    // full[b] (stage b written; 128 producer threads), freed[b] (accumulator
-    // b read; 256 epilogue threads), tabfull[b] (gather entries of the tile
-    // written; 128 producers), tabfree[b] (that tile's windows stored; 256
-    // epilogue threads), rawbar[v] (producer v's input copy landed)
+    // mbarriers: done[c] (products into accumulator c complete; one
+    // commit), full[b] (stage b written; 128 producer threads), freed[c]
+    // (accumulator c read; the 128 threads of an epilogue group), tabfull[b]
+    // (gather entries of a tile of parity b written; 128 producers),
+    // tabfree[b] (that tile's windows stored; 128 epilogue threads),
+    // rawbar[v] (producer v's input copy landed).  Tile i uses accumulator
+    // i mod 3, stage and entry buffer i mod 2.
     uint64_t *done = reinterpret_cast<uint64_t *>(smtc + kSmMisc);
-    uint64_t *full = done + 2;
-    uint64_t *freed = done + 4;
-    uint64_t *tabfull = done + 6;
-    uint64_t *tabfree = done + 8;
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(smtc + kSmMisc + 80);
-    int *gflag = reinterpret_cast<int *>(smtc + kSmMisc + 84);           // [2]: a group's wait gave up
-    float *vsc = reinterpret_cast<float *>(smtc + kSmMisc + 96);        // [4 tiles][4 vectors]
-    uint64_t *rawbar = reinterpret_cast<uint64_t *>(smtc + kSmMisc + 160);   // [4]
+    uint64_t *full = done + 3;
+    uint64_t *freed = done + 5;
+    uint64_t *tabfull = done + 8;
+    uint64_t *tabfree = done + 10;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(smtc + kSmMisc + 96);
+    int *gflag = reinterpret_cast<int *>(smtc + kSmMisc + 100);          // [2]: a group's wait gave up
+    float *vsc = reinterpret_cast<float *>(smtc + kSmMisc + 112);       // [4 tiles][4 vectors]
+    uint64_t *rawbar = reinterpret_cast<uint64_t *>(smtc + kSmMisc + 176);   // [4]
     TabEnt *tabs = reinterpret_cast<TabEnt *>(smtc + kSmTab);           // [2 tiles][2 pairs][kTabT]
     float2 *beams = reinterpret_cast<float2 *>(smtc + kSmBeam);         // [2 pairs][re, im][2048]
     auto train_of = [&](int64_t vec0) { return (int)((ga.vbase + vec0) >> ga.log2F) < ga.P_train; };
@@ -545,10 +551,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) beamspace_tc_kernel(TcArgs a, G
     constexpr float post = 0.022097086912079608f;   // 1/sqrt(2048)
 
     if (tid == 0) {
-        for (int j = 0; j < 2; ++j) {
+        for (int j = 0; j < kTcAcc; ++j) {
             mbar_init(&done[j], 1);
-            mbar_init(&full[j], 128);
             mbar_init(&freed[j], 128);
+        }
+        for (int j = 0; j < 2; ++j) {
+            mbar_init(&full[j], 128);
             mbar_init(&tabfull[j], 128);
             mbar_init(&tabfree[j], 128);
             gflag[j] = 0;
@@ -581,12 +589,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) beamspace_tc_kernel(TcArgs a, G
         float2 *pb = beams + g * (kSmBeamPair / 8);
         for (int i = g; i < nt; i += 2) {
             const unsigned ph = (unsigned)(i >> 1) & 1u;
-            bool ok = mbar_wait_bounded(&done[g], ph);
+            const int c = i % kTcAcc;
+            bool ok = mbar_wait_bounded(&done[c], (unsigned)(i / kTcAcc) & 1u);
             for (int p = 0; p < 2; ++p) {
                 if (ok) {
                     tc_fence_after();
-                    epilogue(tmem + ((uint32_t)(32 * q) << 16) + 128 * g + 32 * p, tws, pb, k,
-                             p == 1 ? &freed[g] : nullptr);
+                    epilogue(tmem + ((uint32_t)(32 * q) << 16) + 128 * c + 32 * p, tws, pb, k,
+                             p == 1 ? &freed[c] : nullptr);
                 } else {
                     gflag[g] = 1;
                 }
@@ -639,7 +648,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) beamspace_tc_kernel(TcArgs a, G
                 fence_proxy_async();   // the reads complete before the slot is refilled by the async proxy
                 __syncwarp();
                 if (i + 3 < nt) prep_fetch(raw, rbar, a.y, vec0_of(i + 3) + v, lane);
-                ok = mbar_wait_bounded(&done[b], (unsigned)(i >> 1) & 1u);
+                ok = mbar_wait_bounded(&done[i % kTcAcc], (unsigned)(i / kTcAcc) & 1u);
                 if (!ok) break;
                 prep_store(pr, sbase + kSmB + b * kSmBStage, vsc + 4 * ((i + 2) & 3), v, lane, post);
                 mbar_arrive(&full[b]);
@@ -647,20 +656,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) beamspace_tc_kernel(TcArgs a, G
         }
         if (!ok && lane == 0) atomicOr(a.err, 1);
     } else {
-        // ---- MMA warp: products of tile i into accumulator i mod 2 once stage
-        // i mod 2 is written and (from tile 2 on) the accumulator has been read
+        // ---- MMA warp: products of tile i into accumulator i mod 3 once stage
+        // i mod 2 is written and (from tile 3 on) the accumulator has been read
         __syncthreads();
         for (int i = 0; i < nt; ++i) {
-            const int b = i & 1;
-            const unsigned u = (unsigned)(i >> 1);
-            bool ok = mbar_wait_bounded(&full[b], u & 1u);
-            if (ok && i >= 2) ok = mbar_wait_bounded(&freed[b], (u - 1) & 1u);
+            const int b = i & 1, c = i % kTcAcc;
+            bool ok = mbar_wait_bounded(&full[b], (unsigned)(i >> 1) & 1u);
+            if (ok && i >= kTcAcc) ok = mbar_wait_bounded(&freed[c], (unsigned)(i / kTcAcc - 1) & 1u);
             if (!ok) {   // the other warps then give up on their waits
                 if (lane == 0) atomicOr(a.err, 1);
                 break;
             }
             tc_fence_after();
-            if (lane == 0) issue_tile(tmem, b, sbase + kSmB + b * kSmBStage, &done[b]);
+            if (lane == 0) issue_tile(tmem, c, sbase + kSmB + b * kSmBStage, &done[c]);
             __syncwarp();
         }
     }
