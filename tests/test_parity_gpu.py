@@ -561,16 +561,25 @@ def test_graph_and_autotune():
     assert plan.device_status() == 0
 
 
+# (W, K, training records): K up to 128 with ragged 16-vector blocks, and
+# K < 8, K not a multiple of the 64-vector stage and K beyond the ring of
+# stages (the ring wraps)
+TC_COV_CASES = {
+    "short": ((1, 2, 3, 5, 8, 9, 12, 15, 16), (1, 7, 17, 40, 64, 65, 100, 127, 128), 1),
+    "wrapping": ((1, 2, 3, 4, 5, 8, 9, 12, 15, 16), (4, 2, 4, 1, 8, 65, 4, 100, 128, 300), 3),
+}
+
+
+@pytest.mark.parametrize("case", list(TC_COV_CASES))
 @pytest.mark.parametrize("precision", [P.BS_PREC_FP16, P.BS_PREC_BF16])
-def test_tensor_core_covariance(precision):
+def test_tensor_core_covariance(precision, case):
     """16-bit windows: the tensor-core covariance equals the FP64 covariance
     of the same (dequantised) windows to COV_TOL, for W = 1..16 and K not a
     multiple of 16 (ragged last k-block)."""
     base = all_configs()["C1"]
-    W = (1, 2, 3, 5, 8, 9, 12, 15, 16)
-    K = (1, 7, 17, 40, 64, 65, 100, 127, 128)
+    W, K, ptr = TC_COV_CASES[case]
     cfg = scaled_config(base, name="tc-cov", N=64, F=512, L=4, M=64, T=len(W), W=W, K=K,
-                        P_tr=1, P_te=1, n_jam=2)
+                        P_tr=ptr, P_te=1, n_jam=2)
     sc = make_scene(cfg)
     res = run_gpu(cfg, sc.x, sc.u_tgt, precision=precision, keep_xc=False)
     for g in range(res.plan.sizes.pairs):
