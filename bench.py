@@ -301,6 +301,8 @@ def run_ours(args):
         ]
 
     graph = None if args.no_graph else P.Graph(plan, b, stream)
+    # kernels one pass launches, read from a captured graph of the pass
+    kernels_per_step = (graph or P.Graph(plan, b, stream)).kernel_count()
 
     def step():
         if graph is not None:
@@ -520,7 +522,7 @@ def run_ours(args):
             "config": dict(workload_desc(cfg), precision=args.precision,
                            parallelism=f"{ws} independent batch(es)"),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": len(stages) * args.steps,
+            "gpu_launches": kernels_per_step * args.steps,
             "timed_as": "CUDA graph of the whole pass" if graph is not None else "bs_run calls",
             "autotune": tune,
             "clocks": clocks, "stages": per_stage, "solve_core_ms": solve_core_ms,

@@ -441,6 +441,9 @@ typedef struct bs_graph bs_graph;
 bs_status bs_graph_create(const bs_plan *plan, const bs_buffers *buf, bs_stream stream, bs_graph **graph);
 bs_status bs_graph_launch(bs_graph *graph, bs_stream stream);
 void      bs_graph_destroy(bs_graph *graph);
+/* Number of kernel nodes in the captured pass (the kernels one launch of
+ * the graph runs), written to *kernels. */
+bs_status bs_graph_kernel_count(const bs_graph *graph, int32_t *kernels);
 
 /* ---------------------------------------------------- learned loading --- */
 /* A small MLP predicts, from a window's covariance estimated with few

@@ -104,6 +104,7 @@ _SIGS = {
     "bs_graph_create": ([_P, ctypes.POINTER(_Buffers), _P, ctypes.POINTER(_P)], ctypes.c_int),
     "bs_graph_launch": ([_P, _P], ctypes.c_int),
     "bs_graph_destroy": ([_P], None),
+    "bs_graph_kernel_count": ([_P, ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
     "bs_status_string": ([ctypes.c_int], ctypes.c_char_p),
     "bs_last_error": ([], ctypes.c_char_p),
 }
@@ -560,6 +561,12 @@ class Graph:
 
     def launch(self, stream):
         _check(lib().bs_graph_launch(self._h, _stream(stream)), "bs_graph_launch")
+
+    def kernel_count(self) -> int:
+        """Kernels one launch of the graph runs (bs_graph_kernel_count)."""
+        n = ctypes.c_int32()
+        _check(lib().bs_graph_kernel_count(self._h, ctypes.byref(n)), "bs_graph_kernel_count")
+        return n.value
 
     def close(self):
         if getattr(self, "_h", None):

@@ -2,6 +2,7 @@
 // kernel launchers of the individual translation units.
 #include <algorithm>
 #include <string>
+#include <vector>
 
 #include "host_chunks.h"
 #include "internal.h"
@@ -199,6 +200,25 @@ bs_status bs_graph_create(const bs_plan *p, const bs_buffers *b, bs_stream strea
 bs_status bs_graph_launch(bs_graph *g, bs_stream stream) {
     BS_REQUIRE(g, "NULL graph");
     return bs::cuda_error(cudaGraphLaunch(g->exec, (cudaStream_t)stream), "graph launch");
+}
+
+bs_status bs_graph_kernel_count(const bs_graph *g, int32_t *kernels) {
+    BS_REQUIRE(g && kernels, "NULL argument");
+    size_t n = 0;
+    cudaError_t e = cudaGraphGetNodes(g->graph, nullptr, &n);
+    if (e != cudaSuccess) return bs::cuda_error(e, "graph nodes");
+    std::vector<cudaGraphNode_t> nodes(n);
+    if (n) e = cudaGraphGetNodes(g->graph, nodes.data(), &n);
+    if (e != cudaSuccess) return bs::cuda_error(e, "graph nodes");
+    int32_t k = 0;
+    for (size_t i = 0; i < n; ++i) {
+        cudaGraphNodeType t;
+        e = cudaGraphNodeGetType(nodes[i], &t);
+        if (e != cudaSuccess) return bs::cuda_error(e, "graph node type");
+        k += t == cudaGraphNodeTypeKernel;
+    }
+    *kernels = k;
+    return BS_OK;
 }
 
 void bs_graph_destroy(bs_graph *g) {

@@ -67,6 +67,7 @@ struct bs_plan {
     int32_t *d_order_w = nullptr;
     int Wmin = 0;
     int64_t nsmall = 0;   // pairs with W <= 16 (the first of order_w)
+    int64_t wstart[34] = {};   // pairs of window size W are slots wstart[W] .. wstart[W + 1] - 1 of order_w
     int *d_head = nullptr;
     bs::CovSolveLaunch cs;
     // kernel variants chosen by bs_autotune_pass (-1: the built-in choice)

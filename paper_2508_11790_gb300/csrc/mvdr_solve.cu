@@ -1,8 +1,9 @@
 // Stand-alone MVDR solve (Eq. BeamCorrMVDR) of every pair from its stored
-// FP64 covariance: one half-warp per pair (W <= 16), eight pairs per CTA,
-// or one warp per pair (16 < W <= 32).  The solve itself (FP32 Cholesky,
-// compensated refinement, FP64 escalation) is solve_pair_fixed() in
-// solve_dev.cuh.
+// FP64 covariance: one launch per window size present, pairs visited in
+// the plan's W-grouped order.  An 8-lane group solves a pair of W <= 8, a
+// half-warp one of 8 < W <= 16, a warp one of 16 < W <= 32.  The solve
+// itself (FP32 Cholesky, compensated refinement, FP64 escalation) is
+// solve_pair_body() in solve_dev.cuh.
 #include <math.h>
 
 #include "common.cuh"
@@ -11,25 +12,44 @@
 
 namespace bs {
 
-constexpr int SOLVE_PAIRS_PER_CTA = 8;
-
-__global__ void __launch_bounds__(SOLVE_PAIRS_PER_CTA * 16, 4)
-    mvdr_solve_kernel(const double2 *__restrict__ R, const int64_t *__restrict__ roff,
-                      const int32_t *__restrict__ Wg, const int64_t *__restrict__ woff,
-                      const float2 *__restrict__ at32, const float2 *__restrict__ atlo,
-                      const double2 *__restrict__ at64, float2 *__restrict__ c, int32_t *__restrict__ info,
-                      int64_t pairs, double kappa_max, int refine, int allow_f64, const int32_t *__restrict__ order,
-                      const float *__restrict__ dpre) {
-    __shared__ double2 scratch[SOLVE_PAIRS_PER_CTA][WMAX][WMAX + 1];
-    const int hw = threadIdx.x >> 4;
-    const int lane = threadIdx.x & 15;
-    const unsigned mask = (threadIdx.x & 16) ? 0xFFFF0000u : 0x0000FFFFu;
-    const int64_t slot = (int64_t)blockIdx.x * SOLVE_PAIRS_PER_CTA + hw;
-    if (slot >= pairs) return;   // uniform over the half-warp
-    const int64_t g = order ? (int64_t)order[slot] : slot;   // pairs grouped by W
+// The pairs of one window size W <= 16, solved by a kernel compiled for
+// that size alone: one kernel holding the bodies of all sixteen sizes
+// behind a switch stalled mostly on instruction fetch.  GW = 8 lanes per
+// pair for W <= 8 (sixteen pairs per CTA), else 16 (eight pairs per CTA).
+template <int WT>
+__global__ void __launch_bounds__(128, 4)
+    mvdr_solve_w_kernel(const double2 *__restrict__ R, const int64_t *__restrict__ roff,
+                        const int64_t *__restrict__ woff, const float2 *__restrict__ at32,
+                        const float2 *__restrict__ atlo, const double2 *__restrict__ at64, float2 *__restrict__ c,
+                        int32_t *__restrict__ info, int64_t slot0, int64_t slot1, double kappa_max, int refine,
+                        int allow_f64, const int32_t *__restrict__ order, const float *__restrict__ dpre) {
+    constexpr int GW = (WT <= 8) ? 8 : 16;
+    constexpr int PPC = 128 / GW;
+    __shared__ double2 scratch[PPC][GW][GW + 1];
+    const int grp = threadIdx.x / GW;
+    const int lane = threadIdx.x % GW;
+    const unsigned mask = (GW == 8) ? (0xFFu << (threadIdx.x & 24)) : ((threadIdx.x & 16) ? 0xFFFF0000u : 0x0000FFFFu);
+    const int64_t slot = slot0 + (int64_t)blockIdx.x * PPC + grp;
+    if (slot >= slot1) return;   // uniform over the group
+    const int64_t g = order ? (int64_t)order[slot] : slot;
     const int64_t wo = woff[g];
-    solve_pair_inline(mask, lane, Wg[g], R + roff[g], at32 + wo, atlo + wo, at64 + wo, c + wo, info + g, kappa_max,
-                      refine, allow_f64, scratch[hw], dpre ? dpre + wo : nullptr);
+    solve_pair_body<WT, GW>(mask, lane, R + roff[g], at32 + wo, atlo + wo, at64 + wo, c + wo, info + g, kappa_max,
+                            refine, allow_f64, scratch[grp], dpre ? dpre + wo : nullptr);
+}
+
+// The pairs of window size WT: slots wstart[WT] .. wstart[WT + 1] - 1 of
+// the W-grouped order (the identity when every pair has that size).
+template <int WT>
+bs_status launch_solve_w(const bs_plan *p, const double2 *R, float2 *c, int32_t *info, cudaStream_t st,
+                         const float *dpre, int refine, int f64) {
+    constexpr int PPC = 128 / ((WT <= 8) ? 8 : 16);
+    const int64_t s0 = p->wstart[WT], s1 = p->wstart[WT + 1];
+    if (s1 <= s0) return BS_OK;
+    const int32_t *order = p->Wmin == p->Wmax ? nullptr : p->d_order_w;
+    const unsigned blocks = (unsigned)((s1 - s0 + PPC - 1) / PPC);
+    mvdr_solve_w_kernel<WT><<<blocks, 128, 0, st>>>(R, p->d_roff, p->d_woff, p->d_at32, p->d_atlo, p->d_at64, c,
+                                                    info, s0, s1, p->cfg.kappa_max, refine, f64, order, dpre);
+    return check_launch("solve (one window size) launch");
 }
 
 // Windows of 17..32 beams: one warp per pair, solved at WT = 24 or 32 with
@@ -153,15 +173,16 @@ bs_status launch_mvdr_solve(const bs_plan *p, const double2 *R, float2 *c, int32
     }
     const int refine = (p->cfg.flags & BS_FLAG_NO_REFINE) ? 0 : 1;
     const int f64 = (p->cfg.flags & BS_FLAG_NO_FP64) ? 0 : 1;
+    // windows of up to 16 beams: one launch per window size present, each of
+    // a kernel compiled for that size alone
+#define BS_SOLVE_W(n) \
+    if (bs_status s = launch_solve_w<n>(p, R, c, info, st, dpre, refine, f64)) return s;
+    BS_SOLVE_W(1) BS_SOLVE_W(2) BS_SOLVE_W(3) BS_SOLVE_W(4) BS_SOLVE_W(5) BS_SOLVE_W(6) BS_SOLVE_W(7)
+    BS_SOLVE_W(8) BS_SOLVE_W(9) BS_SOLVE_W(10) BS_SOLVE_W(11) BS_SOLVE_W(12) BS_SOLVE_W(13)
+    BS_SOLVE_W(14) BS_SOLVE_W(15) BS_SOLVE_W(16)
+#undef BS_SOLVE_W
     const int32_t *order = p->Wmin == p->Wmax ? nullptr : p->d_order_w;   // pairs grouped by W, smallest first
-    const int64_t nsmall = p->nsmall;                                       // pairs with W <= 16 come first
-    if (nsmall > 0) {
-        const unsigned blocks = (unsigned)((nsmall + SOLVE_PAIRS_PER_CTA - 1) / SOLVE_PAIRS_PER_CTA);
-        mvdr_solve_kernel<<<blocks, SOLVE_PAIRS_PER_CTA * 16, 0, st>>>(
-            R, p->d_roff, p->d_Wg, p->d_woff, p->d_at32, p->d_atlo, p->d_at64, c, info, nsmall, p->cfg.kappa_max,
-            refine, f64, order, dpre);
-        if (bs_status s = check_launch("solve launch")) return s;
-    }
+    const int64_t nsmall = p->nsmall;   // pairs with W <= 16 come first
     if (nsmall < G) {
         constexpr size_t smem = WIDE_WARPS * sizeof(WideSmem);
         static PerDevice attr;

@@ -372,6 +372,8 @@ bs_status bs_plan_create(bs_plan **out, const bs_config *cfg) {
                      [&](int32_t x, int32_t y) { return p->Wg[x] < p->Wg[y]; });
     p->Wmin = *std::min_element(p->Wg.begin(), p->Wg.end());
     p->nsmall = std::count_if(p->Wg.begin(), p->Wg.end(), [](int32_t w) { return w <= 16; });
+    for (int w = 1; w <= 33; ++w)   // order_w is sorted by W
+        p->wstart[w] = p->wstart[w - 1] + std::count(p->Wg.begin(), p->Wg.end(), w - 1);
 
     cudaGetDevice(&p->device);
     bs_status st = BS_OK;

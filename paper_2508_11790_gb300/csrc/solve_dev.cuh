@@ -400,27 +400,6 @@ static __device__ __noinline__ void solve_pair_fixed(unsigned mask, int lane, co
     solve_pair_body<WT, GW>(mask, lane, Rg, a32g, alog, a64g, c, info, kappa_max, refine, allow_f64, scratch, dg);
 }
 
-// The solve of every window size inlined into the calling kernel (the
-// stand-alone solve: its pairs are grouped by W, so the warps resident on
-// an SM run one body; with calls instead, every call saved and restored
-// the caller's live registers in local memory).
-__device__ __forceinline__ void solve_pair_inline(unsigned mask, int lane, int W, const double2 *Rg,
-                                                  const float2 *__restrict__ a32g, const float2 *__restrict__ alog,
-                                                  const double2 *__restrict__ a64g, float2 *__restrict__ c,
-                                                  int32_t *__restrict__ info, double kappa_max, int refine,
-                                                  int allow_f64, double2 (*scratch)[WMAX + 1],
-                                                  const float *__restrict__ dg) {
-#define BS_SOLVE_CASE(n) \
-    case n: solve_pair_body<n>(mask, lane, Rg, a32g, alog, a64g, c, info, kappa_max, refine, allow_f64, scratch, dg); break;
-    switch (W) {
-        BS_SOLVE_CASE(1) BS_SOLVE_CASE(2) BS_SOLVE_CASE(3) BS_SOLVE_CASE(4)
-        BS_SOLVE_CASE(5) BS_SOLVE_CASE(6) BS_SOLVE_CASE(7) BS_SOLVE_CASE(8)
-        BS_SOLVE_CASE(9) BS_SOLVE_CASE(10) BS_SOLVE_CASE(11) BS_SOLVE_CASE(12)
-        BS_SOLVE_CASE(13) BS_SOLVE_CASE(14) BS_SOLVE_CASE(15) default: BS_SOLVE_CASE(16)
-    }
-#undef BS_SOLVE_CASE
-}
-
 // R stored as FP64 (global or shared memory); dispatches on W to the solve
 // compiled for that window size.
 __device__ __forceinline__ void solve_pair(unsigned mask, int lane, int W, const double2 *Rg,
