@@ -368,6 +368,46 @@ def uneven_small_config():
                          P_tr=8, P_te=2, n_jam=4)
 
 
+@pytest.mark.parametrize("precond", [False, True])
+def test_escalation_every_pair(precond):
+    """Stand-alone solve with every pair escalated (kappa_max just above 1):
+    1536 pairs, W from 2 to 16 in both lane-group widths, each solved again
+    on the escalation path.  Weights against the oracle's FP64 solve of the
+    GPU's own covariances (Eq. BeamCorrMVDR; with a diagonal preconditioner
+    the same weights in exact arithmetic), info -2."""
+    base = all_configs()["C4"]
+    rng = np.random.default_rng(11)
+    T = 24
+    W = tuple(int(w) for w in rng.choice([2, 3, 5, 8, 9, 12, 16], size=T))
+    K = tuple(int(rng.integers(2 * w, 6 * w + 1)) for w in W)
+    cfg = scaled_config(base, name="escalate-all", N=256, F=1024, L=64, M=512, T=T, W=W, K=K, P_te=1, n_jam=4)
+    sc = make_scene(cfg)
+    plan = P.Plan.from_scene_config(cfg, sc.u_tgt, kappa_max=1.0001)
+    assert plan.sizes.pairs == 1536
+    b = P.alloc_buffers(plan)
+    b.x.copy_(torch.from_numpy(sc.x.reshape(-1)))
+    P.bs_channelize(plan, b.x, b.xc)
+    P.bs_beamspace(plan, b.xc, b.z_train, b.z_test)
+    P.bs_window_cov(plan, b.z_train, b.R)
+    b.info.fill_(99)
+    off = plan.offsets()
+    if precond:
+        d = (2.0 ** np.random.default_rng(12).uniform(-6, 6, size=plan.sizes.c_elems)).astype(np.float32)
+        P.bs_mvdr_solve_precond(plan, b.R, torch.from_numpy(d).cuda(), b.c, b.info)
+    else:
+        P.bs_mvdr_solve(plan, b.R, b.c, b.info)
+    torch.cuda.synchronize()
+    R, c, info = b.R.cpu().numpy(), b.c.cpu().numpy(), b.info.cpu().numpy()
+    assert (info == -2).all(), np.unique(info, return_counts=True)
+    worst = 0.0
+    for g in range(plan.sizes.pairs):
+        Wg = int(off["W"][g])
+        Rg = R[off["roff"][g]:off["roff"][g + 1]].reshape(Wg, Wg)
+        a = off["a_tilde"][off["woff"][g]:off["woff"][g + 1]]
+        worst = max(worst, rel(c[off["woff"][g]:off["woff"][g + 1]], O.mvdr_weights(Rg, a)))
+    assert worst <= SOLVE_TOL, worst
+
+
 @pytest.mark.parametrize("precision", [P.BS_PREC_FP32, P.BS_PREC_FP16])
 def test_fused_cov_solve_matches_unfused(precision):
     """bs_cov_solve (persistent, work queue) against bs_window_cov +
