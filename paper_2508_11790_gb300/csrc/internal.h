@@ -58,6 +58,11 @@ struct bs_plan {
     static constexpr int kHostChunks = 8;
     cudaStream_t copy_st = nullptr;
     cudaEvent_t ev_start = nullptr, ev_chunk[kHostChunks] = {};
+    // the stand-alone solve's window-size launches run on `stream` and these
+    // side streams (forked from and joined back into `stream`)
+    static constexpr int kSolveStreams = 4;
+    cudaStream_t solve_st[kSolveStreams] = {};
+    cudaEvent_t ev_fork = nullptr, ev_join[kSolveStreams] = {};
     int num_sms = 0;
     // fused covariance + solve: queue order (decreasing W^2 K), workspace head
     std::vector<int32_t> order;

@@ -174,16 +174,36 @@ bs_status launch_mvdr_solve(const bs_plan *p, const double2 *R, float2 *c, int32
     const int refine = (p->cfg.flags & BS_FLAG_NO_REFINE) ? 0 : 1;
     const int f64 = (p->cfg.flags & BS_FLAG_NO_FP64) ? 0 : 1;
     // windows of up to 16 beams: one launch per window size present, each of
-    // a kernel compiled for that size alone
-#define BS_SOLVE_W(n) \
-    if (bs_status s = launch_solve_w<n>(p, R, c, info, st, dpre, refine, f64)) return s;
-    BS_SOLVE_W(1) BS_SOLVE_W(2) BS_SOLVE_W(3) BS_SOLVE_W(4) BS_SOLVE_W(5) BS_SOLVE_W(6) BS_SOLVE_W(7)
-    BS_SOLVE_W(8) BS_SOLVE_W(9) BS_SOLVE_W(10) BS_SOLVE_W(11) BS_SOLVE_W(12) BS_SOLVE_W(13)
-    BS_SOLVE_W(14) BS_SOLVE_W(15) BS_SOLVE_W(16)
+    // a kernel compiled for that size alone.  The launches are independent
+    // (disjoint pairs): with several, they are spread over `st` and the
+    // plan's side streams (forked from `st` and joined back into it; under
+    // graph capture, parallel branches), so that one launch's tail overlaps
+    // the others' work.
+    const int64_t nsmall = p->nsmall;   // pairs with W <= 16 come first
+    int nlaunch = nsmall < G ? 1 : 0;
+    for (int w = 1; w <= 16; ++w) nlaunch += p->wstart[w + 1] > p->wstart[w];
+    const int nst = nlaunch < 1 + bs_plan::kSolveStreams ? nlaunch : 1 + bs_plan::kSolveStreams;
+    if (nst > 1) {
+        cudaError_t e = cudaEventRecord(p->ev_fork, st);
+        for (int k = 0; k + 1 < nst && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(p->solve_st[k], p->ev_fork, 0);
+        if (e != cudaSuccess) return cuda_error(e, "solve fork");
+    }
+    int li = 0;   // launches issued; launch i goes to stream i mod nst
+    auto next_stream = [&]() -> cudaStream_t {
+        const int k = li++ % (nst > 0 ? nst : 1);
+        return k == 0 ? st : p->solve_st[k - 1];
+    };
+    // largest windows first: the longest launches start first on their streams
+#define BS_SOLVE_W(n)                                                                                  \
+    if (p->wstart[n + 1] > p->wstart[n])                                                               \
+        if (bs_status s = launch_solve_w<n>(p, R, c, info, next_stream(), dpre, refine, f64)) return s;
+    BS_SOLVE_W(16) BS_SOLVE_W(15) BS_SOLVE_W(14) BS_SOLVE_W(13) BS_SOLVE_W(12) BS_SOLVE_W(11)
+    BS_SOLVE_W(10) BS_SOLVE_W(9) BS_SOLVE_W(8) BS_SOLVE_W(7) BS_SOLVE_W(6) BS_SOLVE_W(5) BS_SOLVE_W(4)
+    BS_SOLVE_W(3) BS_SOLVE_W(2) BS_SOLVE_W(1)
 #undef BS_SOLVE_W
     const int32_t *order = p->Wmin == p->Wmax ? nullptr : p->d_order_w;   // pairs grouped by W, smallest first
-    const int64_t nsmall = p->nsmall;   // pairs with W <= 16 come first
     if (nsmall < G) {
+        const cudaStream_t ws = next_stream();
         constexpr size_t smem = WIDE_WARPS * sizeof(WideSmem);
         static PerDevice attr;
         if (bs_status s = attr.get([](int *) {
@@ -193,10 +213,18 @@ bs_status launch_mvdr_solve(const bs_plan *p, const double2 *R, float2 *c, int32
             }))
             return s;
         const unsigned blocks = (unsigned)((G - nsmall + WIDE_WARPS - 1) / WIDE_WARPS);
-        mvdr_solve_wide_kernel<<<blocks, WIDE_WARPS * 32, smem, st>>>(
+        mvdr_solve_wide_kernel<<<blocks, WIDE_WARPS * 32, smem, ws>>>(
             R, p->d_roff, p->d_Wg, p->d_woff, p->d_at32, p->d_atlo, p->d_at64, c, info, nsmall, G, p->cfg.kappa_max,
             refine, f64, order, dpre);
         if (bs_status s = check_launch("solve (wide) launch")) return s;
+    }
+    if (nst > 1) {   // join: `st` waits for every side stream's launches
+        cudaError_t e = cudaSuccess;
+        for (int k = 0; k + 1 < nst && e == cudaSuccess; ++k) {
+            e = cudaEventRecord(p->ev_join[k], p->solve_st[k]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(st, p->ev_join[k], 0);
+        }
+        if (e != cudaSuccess) return cuda_error(e, "solve join");
     }
     return BS_OK;
 }

@@ -173,6 +173,11 @@ void bs_plan_destroy(bs_plan *p) {
         if (e) cudaEventDestroy(e);
     if (p->ev_start) cudaEventDestroy(p->ev_start);
     if (p->copy_st) cudaStreamDestroy(p->copy_st);
+    for (int k = 0; k < bs_plan::kSolveStreams; ++k) {
+        if (p->solve_st[k]) cudaStreamDestroy(p->solve_st[k]);
+        if (p->ev_join[k]) cudaEventDestroy(p->ev_join[k]);
+    }
+    if (p->ev_fork) cudaEventDestroy(p->ev_fork);
     delete p;
 }
 
@@ -400,6 +405,11 @@ bs_status bs_plan_create(bs_plan **out, const bs_config *cfg) {
     if (!st) st = upload(&p->d_head, std::vector<int>(1, 0));
     if (!st) st = bs::cuda_error(cudaStreamCreateWithFlags(&p->copy_st, cudaStreamNonBlocking), "copy stream");
     if (!st) st = bs::cuda_error(cudaEventCreateWithFlags(&p->ev_start, cudaEventDisableTiming), "event");
+    if (!st) st = bs::cuda_error(cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming), "event");
+    for (int k = 0; k < bs_plan::kSolveStreams && !st; ++k) {
+        st = bs::cuda_error(cudaStreamCreateWithFlags(&p->solve_st[k], cudaStreamNonBlocking), "solve stream");
+        if (!st) st = bs::cuda_error(cudaEventCreateWithFlags(&p->ev_join[k], cudaEventDisableTiming), "event");
+    }
     for (int k = 0; k < bs_plan::kHostChunks && !st; ++k)
         st = bs::cuda_error(cudaEventCreateWithFlags(&p->ev_chunk[k], cudaEventDisableTiming), "event");
     if (!st) st = bs::cuda_error(cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device),
