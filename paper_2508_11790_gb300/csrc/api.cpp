@@ -158,6 +158,14 @@ bs_status bs_run(const bs_plan *p, const bs_buffers *b, bs_stream stream) {
     if ((s = bs_beamspace(p, b->xc, b->z_train, b->z_test, stream))) return s;
     if (use_fused(p)) {
         if ((s = bs_cov_solve(p, b->z_train, nullptr, b->R, b->c, b->info, stream))) return s;
+    } else if (bs::cov_solve_chains_apply(p)) {
+        // several window sizes on the warp-per-pair covariance: one
+        // covariance + solve chain per size, the chains in parallel
+        BS_REQUIRE(b->z_train && b->R && b->c && b->info, "NULL buffer");
+        if ((s = check_device(p))) return s;
+        if ((s = bs::launch_cov_solve_chains(p, b->z_train, (double2 *)b->R, (float2 *)b->c, b->info,
+                                             (cudaStream_t)stream)))
+            return s;
     } else {
         if ((s = bs_window_cov(p, b->z_train, nullptr, b->R, stream))) return s;
         if ((s = bs_mvdr_solve(p, b->R, b->c, b->info, stream))) return s;

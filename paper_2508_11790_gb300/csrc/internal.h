@@ -122,6 +122,17 @@ bs_status launch_beamspace(const bs_plan *p, const float2 *xc, void *ztr, float2
                            int np = -1);
 bs_status launch_beamspace_full(const bs_plan *p, const float2 *y, int64_t nvec, float2 *yb,
                                 cudaStream_t st);
+// The covariance launcher's choice for this plan is the warp-per-pair kernel.
+bool window_cov_uses_warp(const bs_plan *p);
+// Warp-per-pair covariance of slots [slot0, slot1) of `order` (pair order if null).
+bs_status launch_window_cov_warp(const bs_plan *p, const void *ztr, const float *delta, double2 *R,
+                                 cudaStream_t st, int64_t slot0, int64_t slot1, const int32_t *order);
+// Covariance and stand-alone solve as one chain per window size, the chains
+// in parallel (plan side streams); applies to plans whose covariance takes
+// the warp-per-pair kernel, with several window sizes, all at most 16 beams.
+bool cov_solve_chains_apply(const bs_plan *p);
+bs_status launch_cov_solve_chains(const bs_plan *p, const void *ztr, double2 *R, float2 *c, int32_t *info,
+                                  cudaStream_t st);
 bs_status launch_window_cov(const bs_plan *p, const void *ztr, const float *delta, double2 *R,
                             cudaStream_t st);
 bs_status launch_window_cov_mma(const bs_plan *p, const void *ztr, const float *delta, double2 *R,

@@ -163,6 +163,58 @@ __global__ void plain_solve_kernel(const double2 *__restrict__ R, const int64_t 
     info[g] = 0;
 }
 
+// Fork: the first nst - 1 side streams of the plan wait for `st`.
+static bs_status fork_streams(const bs_plan *p, cudaStream_t st, int nst) {
+    if (nst <= 1) return BS_OK;
+    cudaError_t e = cudaEventRecord(p->ev_fork, st);
+    for (int k = 0; k + 1 < nst && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(p->solve_st[k], p->ev_fork, 0);
+    return e == cudaSuccess ? BS_OK : cuda_error(e, "solve fork");
+}
+// Join: `st` waits for everything issued to those side streams.
+static bs_status join_streams(const bs_plan *p, cudaStream_t st, int nst) {
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k + 1 < nst && e == cudaSuccess; ++k) {
+        e = cudaEventRecord(p->ev_join[k], p->solve_st[k]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, p->ev_join[k], 0);
+    }
+    return e == cudaSuccess ? BS_OK : cuda_error(e, "solve join");
+}
+static int window_classes(const bs_plan *p) {
+    int n = 0;
+    for (int w = 1; w <= 16; ++w) n += p->wstart[w + 1] > p->wstart[w];
+    return n;
+}
+
+bool cov_solve_chains_apply(const bs_plan *p) {
+    return !(p->cfg.flags & BS_FLAG_PLAIN) && p->nsmall == p->pairs && window_classes(p) > 1 &&
+           window_cov_uses_warp(p);
+}
+
+bs_status launch_cov_solve_chains(const bs_plan *p, const void *ztr, double2 *R, float2 *c, int32_t *info,
+                                  cudaStream_t st) {
+    const int refine = (p->cfg.flags & BS_FLAG_NO_REFINE) ? 0 : 1;
+    const int f64 = (p->cfg.flags & BS_FLAG_NO_FP64) ? 0 : 1;
+    const int ncls = window_classes(p);
+    const int nst = ncls < 1 + bs_plan::kSolveStreams ? ncls : 1 + bs_plan::kSolveStreams;
+    if (bs_status s = fork_streams(p, st, nst)) return s;
+    int li = 0;
+    // one chain per window size (covariance of its pairs, then their solve),
+    // largest windows first, chain i on stream i mod nst
+#define BS_CHAIN(n)                                                                                          \
+    if (p->wstart[n + 1] > p->wstart[n]) {                                                                   \
+        const int k_ = li++ % nst;                                                                           \
+        const cudaStream_t s_ = k_ == 0 ? st : p->solve_st[k_ - 1];                                          \
+        if (bs_status s = launch_window_cov_warp(p, ztr, nullptr, R, s_, p->wstart[n], p->wstart[n + 1],     \
+                                                 p->d_order_w))                                              \
+            return s;                                                                                        \
+        if (bs_status s = launch_solve_w<n>(p, R, c, info, s_, nullptr, refine, f64)) return s;              \
+    }
+    BS_CHAIN(16) BS_CHAIN(15) BS_CHAIN(14) BS_CHAIN(13) BS_CHAIN(12) BS_CHAIN(11) BS_CHAIN(10) BS_CHAIN(9)
+    BS_CHAIN(8) BS_CHAIN(7) BS_CHAIN(6) BS_CHAIN(5) BS_CHAIN(4) BS_CHAIN(3) BS_CHAIN(2) BS_CHAIN(1)
+#undef BS_CHAIN
+    return join_streams(p, st, nst);
+}
+
 bs_status launch_mvdr_solve(const bs_plan *p, const double2 *R, float2 *c, int32_t *info, cudaStream_t st,
                             const float *dpre) {
     const int64_t G = p->pairs;
@@ -180,14 +232,9 @@ bs_status launch_mvdr_solve(const bs_plan *p, const double2 *R, float2 *c, int32
     // graph capture, parallel branches), so that one launch's tail overlaps
     // the others' work.
     const int64_t nsmall = p->nsmall;   // pairs with W <= 16 come first
-    int nlaunch = nsmall < G ? 1 : 0;
-    for (int w = 1; w <= 16; ++w) nlaunch += p->wstart[w + 1] > p->wstart[w];
+    const int nlaunch = (nsmall < G ? 1 : 0) + window_classes(p);
     const int nst = nlaunch < 1 + bs_plan::kSolveStreams ? nlaunch : 1 + bs_plan::kSolveStreams;
-    if (nst > 1) {
-        cudaError_t e = cudaEventRecord(p->ev_fork, st);
-        for (int k = 0; k + 1 < nst && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(p->solve_st[k], p->ev_fork, 0);
-        if (e != cudaSuccess) return cuda_error(e, "solve fork");
-    }
+    if (bs_status s = fork_streams(p, st, nst)) return s;
     int li = 0;   // launches issued; launch i goes to stream i mod nst
     auto next_stream = [&]() -> cudaStream_t {
         const int k = li++ % (nst > 0 ? nst : 1);
@@ -218,15 +265,7 @@ bs_status launch_mvdr_solve(const bs_plan *p, const double2 *R, float2 *c, int32
             refine, f64, order, dpre);
         if (bs_status s = check_launch("solve (wide) launch")) return s;
     }
-    if (nst > 1) {   // join: `st` waits for every side stream's launches
-        cudaError_t e = cudaSuccess;
-        for (int k = 0; k + 1 < nst && e == cudaSuccess; ++k) {
-            e = cudaEventRecord(p->ev_join[k], p->solve_st[k]);
-            if (e == cudaSuccess) e = cudaStreamWaitEvent(st, p->ev_join[k], 0);
-        }
-        if (e != cudaSuccess) return cuda_error(e, "solve join");
-    }
-    return BS_OK;
+    return join_streams(p, st, nst);   // `st` waits for every side stream's launches
 }
 
 }  // namespace bs

@@ -287,12 +287,14 @@ __global__ void __launch_bounds__(COVW_WARPS * 32)
     window_cov_warp_kernel(const void *__restrict__ z, const int64_t *__restrict__ ztr_off,
                            const int32_t *__restrict__ Wg, const int32_t *__restrict__ Kg,
                            const int64_t *__restrict__ roff, const float *__restrict__ delta_pair, DF delta,
-                           float inv_sc, double2 *__restrict__ R, int64_t pairs) {
+                           float inv_sc, double2 *__restrict__ R, int64_t slot0, int64_t slot1,
+                           const int32_t *__restrict__ order) {
     constexpr int ES = (PREC == BS_PREC_FP32) ? 8 : 4;   // bytes per stored element
     __shared__ __align__(16) unsigned char stage[COVW_WARPS][COVW_CH * WMAX_COV * ES];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t g = (int64_t)blockIdx.x * COVW_WARPS + warp;
-    if (g >= pairs) return;   // uniform per warp; no CTA barrier below
+    const int64_t slot = slot0 + (int64_t)blockIdx.x * COVW_WARPS + warp;
+    if (slot >= slot1) return;   // uniform per warp; no CTA barrier below
+    const int64_t g = order ? (int64_t)order[slot] : slot;   // pairs [slot0, slot1) of `order`, or in pair order
     const int W = Wg[g], K = Kg[g];
     unsigned char *sb = stage[warp];
     const unsigned char *zg = reinterpret_cast<const unsigned char *>(z) + ztr_off[g] * ES;
@@ -330,6 +332,39 @@ __global__ void plain_cov_kernel(const float2 *__restrict__ z, const int64_t *__
     R[roff[g] + i * W + j] = make_double2((double)ar, (double)ai);
 }
 
+bool window_cov_uses_warp(const bs_plan *p) {
+    if (p->cfg.flags & BS_FLAG_PLAIN) return false;
+    const bool wide = p->Wmax > WMAX_COV;
+    const int tv = p->tune_cov;
+    const bool mma_ok = !wide && p->cfg.precision != BS_PREC_FP32;
+    if (mma_ok && (tv == 2 || (tv < 0 && !(p->cfg.flags & BS_FLAG_SIMT_COV)))) return false;
+    const bool warp_ok = !wide && p->Kmax <= 128;
+    return warp_ok && (tv == 1 || (tv < 0 && p->pairs >= 4 * (int64_t)p->num_sms));
+}
+
+bs_status launch_window_cov_warp(const bs_plan *p, const void *ztr, const float *delta, double2 *R,
+                                 cudaStream_t st, int64_t slot0, int64_t slot1, const int32_t *order) {
+    if (slot1 <= slot0) return BS_OK;
+    const unsigned blocks = (unsigned)((slot1 - slot0 + COVW_WARPS - 1) / COVW_WARPS);
+    const DF dl = df_from_double(p->cfg.delta);
+    const float inv_sc = 1.0f / p->cfg.store_scale;
+    switch (p->cfg.precision) {
+        case BS_PREC_FP32:
+            window_cov_warp_kernel<BS_PREC_FP32><<<blocks, COVW_WARPS * 32, 0, st>>>(
+                ztr, p->d_ztr_off, p->d_Wg, p->d_Kg, p->d_roff, delta, dl, 1.0f, R, slot0, slot1, order);
+            break;
+        case BS_PREC_FP16:
+            window_cov_warp_kernel<BS_PREC_FP16><<<blocks, COVW_WARPS * 32, 0, st>>>(
+                ztr, p->d_ztr_off, p->d_Wg, p->d_Kg, p->d_roff, delta, dl, inv_sc, R, slot0, slot1, order);
+            break;
+        default:
+            window_cov_warp_kernel<BS_PREC_BF16><<<blocks, COVW_WARPS * 32, 0, st>>>(
+                ztr, p->d_ztr_off, p->d_Wg, p->d_Kg, p->d_roff, delta, dl, inv_sc, R, slot0, slot1, order);
+            break;
+    }
+    return check_launch("covariance (warp per pair) launch");
+}
+
 bs_status launch_window_cov(const bs_plan *p, const void *ztr, const float *delta, double2 *R,
                             cudaStream_t st) {
     const unsigned G = (unsigned)p->pairs;
@@ -346,30 +381,11 @@ bs_status launch_window_cov(const bs_plan *p, const void *ztr, const float *delt
     if (wide && p->Wmax > 32) return set_error(BS_EUNSUPPORTED, "W > 32");
     const int tv = p->tune_cov;   // a variant chosen by bs_autotune_pass, where it applies
     const bool mma_ok = !wide && p->cfg.precision != BS_PREC_FP32;
-    const bool warp_ok = !wide && p->Kmax <= 128;
     if (mma_ok && (tv == 2 || (tv < 0 && !(p->cfg.flags & BS_FLAG_SIMT_COV))))
         return launch_window_cov_mma(p, ztr, delta, R, st);
     const float inv_sc = 1.0f / p->cfg.store_scale;
     // warp per pair: short streams over enough pairs to fill the GPU by warps
-    if (warp_ok && (tv == 1 || (tv < 0 && p->pairs >= 4 * (int64_t)p->num_sms))) {
-        const unsigned blocks = (unsigned)((p->pairs + COVW_WARPS - 1) / COVW_WARPS);
-        const DF dl = df_from_double(p->cfg.delta);
-        switch (p->cfg.precision) {
-            case BS_PREC_FP32:
-                window_cov_warp_kernel<BS_PREC_FP32><<<blocks, COVW_WARPS * 32, 0, st>>>(
-                    ztr, p->d_ztr_off, p->d_Wg, p->d_Kg, p->d_roff, delta, dl, 1.0f, R, p->pairs);
-                break;
-            case BS_PREC_FP16:
-                window_cov_warp_kernel<BS_PREC_FP16><<<blocks, COVW_WARPS * 32, 0, st>>>(
-                    ztr, p->d_ztr_off, p->d_Wg, p->d_Kg, p->d_roff, delta, dl, inv_sc, R, p->pairs);
-                break;
-            default:
-                window_cov_warp_kernel<BS_PREC_BF16><<<blocks, COVW_WARPS * 32, 0, st>>>(
-                    ztr, p->d_ztr_off, p->d_Wg, p->d_Kg, p->d_roff, delta, dl, inv_sc, R, p->pairs);
-                break;
-        }
-        return check_launch("covariance (warp per pair) launch");
-    }
+    if (window_cov_uses_warp(p)) return launch_window_cov_warp(p, ztr, delta, R, st, 0, p->pairs, nullptr);
     switch (p->cfg.precision) {
         case BS_PREC_FP32:
             window_cov_kernel<BS_PREC_FP32><<<G, COV_THREADS, 0, st>>>(
