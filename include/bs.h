@@ -37,7 +37,11 @@
  *      covariance         : W_g * W_g per pair, [i][j] row-major
  *    bs_plan_sizes() returns the totals and bs_plan_offsets() the offsets.
  *  - Not thread-safe per plan if two threads launch on one plan with
- *    different buffers at the same time (plan workspace is shared).
+ *    different buffers at the same time (plan workspace is shared).  The
+ *    same holds for two streams: bs_run_host and the stand-alone solve fork
+ *    work onto streams and events the plan owns (joined back into the
+ *    caller's stream before they return), so calls on one plan are issued
+ *    one after another, in stream order.
  */
 #ifndef BS_H
 #define BS_H
